@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the GDGS view-synthesis path (splat gradients + Poisson solve).
+
+Default workload: 200k edge-concentrated gradient Gaussians on 20 random boxes and
+spheres, one 1920x1080 view, 3 channels, multigrid to relative residual 1e-6,
+mean 0.5 per channel (synthetic, seeded). A step renders one view.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gdgs|reference]
+
+One JSON line on rank 0. Multi-GPU runs are replicas (views are independent):
+each rank renders its own views and value = all views / max-over-ranks time.
+The reference arm times the FP64 CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "prims1080p": "200k gradient Gaussians on the surfaces of 20 boxes/spheres (90%) + 10% "
+                  "uniform, log-scales N(-5,0.7), gradients Laplace(0,0.1) along the projected "
+                  "normal; 1920x1080, 3 channels, multigrid V(2,2) to rel. residual 1e-6, mean 0.5",
+    "tiny64": "1000 gradient Gaussians, 64x64, 3 channels, rtol 1e-8, mean 0.5",
+    "prims4k": "1M gradient Gaussians on 50 primitives, 3840x2160, 3 channels, rtol 1e-6",
+}
+METRIC = "1080p views/s (splat+Poisson, FP32 path, rel. residual <= 1e-6)"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.out = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            txt = ""
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in txt.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,
+                      n_pairs: int) -> float:
+    """Bytes each kernel must move per view (ideal single pass, no re-reads)."""
+    px = C * H * W
+    if kernel == "mg0_down":   # k = 0: rho in, e0 + f1 out; k > 0: also u (hi, lo) in
+        return px * (4 + 4 + 1) + cycles * px * 8
+    if kernel == "mg0_up":     # e0, rho, coarse e1 in, u (hi, lo) out; k > 0: u in
+        return cycles * px * (4 + 4 + 1 + 8) + max(cycles - 1, 0) * px * 8
+    if kernel == "divergence":
+        return px * (8 + 4)
+    if kernel == "finalize":
+        return px * (8 + 4)
+    if kernel == "raster":     # splat records + index per pair, maps out
+        return n_pairs * (4 + 32 + 8 * C) / 1.0 + px * 8
+    if kernel == "project":
+        return n_gauss * (4 * (3 + 3 + 4 + 1 + 2 * C) + 16 + 16 + 4 + 8)
+    return 0.0
+
+
+def make_workload(name):
+    from paper_2405_05446_gb300 import scenes as S
+    return S.workload(name)
+
+
+def run_reference(args, rank, world):
+    """FP64 oracle on the host cores: --steps views after --warmup views (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    O.build()
+    scene, cam, mean, rtol = make_workload(args.workload)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        O.render_view(scene, cam, mean, nthreads=cores)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.render_view(scene, cam, mean, nthreads=cores)
+        t.append(time.perf_counter() - t0)
+    value = len(t) / sum(t)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "global_batch": 1, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(t)} full views of {args.workload} "
+                                       "(box-filtered composite + DCT Neumann solve, FP64)"},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "p50_ms": 1e3 * statistics.median(t), "p99_ms": 1e3 * max(t)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gdgs", choices=["gdgs", "reference"])
+    ap.add_argument("--workload", default="prims1080p", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-views", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2405_05446_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2405_05446_gb300 as G
+
+    scene, cam, mean, rtol = make_workload(args.workload)
+    C, H, W = scene.channels, cam.height, cam.width
+    sopts = G.solver_opts(rtol=rtol)
+    r = G.Renderer(scene.n, C, W, H, sopts=sopts, device=dev)
+    g = G.gaussians_to_device(scene, dev)
+    out = torch.empty((C, H, W), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        r.render_view(g, cam, mean, out)
+    st = r.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"render failed: {st}")
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd and cvd.split(",")[local].strip().isdigit():
+        gpu_index = int(cvd.split(",")[local])
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = G.kernel_launch_count()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.render_view(g, cam, mean, out)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    launches = G.kernel_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    per = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(per)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = world * args.steps / (total_ms_max / 1e3)
+    st = r.stats()
+
+    # end to end through the public API with host buffers: pinned H2D of the scene,
+    # the render, D2H of the image, all inside the timed region
+    host = {k: torch.as_tensor(getattr(scene, k)).pin_memory() for k in
+            ("mean", "scale", "quat", "opacity", "grad")}
+    host_img = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
+    dev_in = G.DeviceGaussians(*(torch.empty_like(host[k], device=dev) for k in
+                                 ("mean", "scale", "quat", "opacity", "grad")))
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = host_img.numel() * 4
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        for k in ("mean", "scale", "quat", "opacity", "grad"):
+            getattr(dev_in, k).copy_(host[k], non_blocking=True)
+        r.render_view(dev_in, cam, mean, out)
+        host_img.copy_(out, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps / (float(te.item()) / 1e3)
+
+    # per-kernel CUDA-event times (outside the timed region)
+    G.profile_begin()
+    for _ in range(args.profile_views):
+        flush.zero_()
+        r.render_view(g, cam, mean, out)
+    torch.cuda.synchronize()
+    prof = G.profile_end()
+
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or HBM_FALLBACK_GBS
+    nv = args.profile_views
+    tot = sum(ms for _, ms in prof.values())
+    kernels = {k: {"launches_per_view": n / nv, "ms_per_view": ms / nv,
+                   "share": ms / tot if tot else 0.0} for k, (n, ms) in sorted(
+        prof.items(), key=lambda kv: -kv[1][1])}
+    hbm_kernels = [k for k in kernels if algorithmic_bytes(k, C, H, W, st["cycles"], scene.n,
+                                                            st["n_pairs"]) > 0 and k != "raster"]
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    roof_k = dom if dom in hbm_kernels else max(hbm_kernels, key=lambda k: kernels[k]["share"])
+    nbytes = algorithmic_bytes(roof_k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
+    ms = kernels[roof_k]["ms_per_view"]
+    achieved = nbytes / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": roof_k, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
+                "algorithmic_bytes_per_view": nbytes, "traffic": None,
+                "dominant_kernel": dom, "dominant_share": kernels[dom]["share"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed views (256 MB write)"},
+            "mpix_per_s": value * W * H / 1e6,
+            "p50_ms": statistics.median(per), "p99_ms": float(np.percentile(per, 99)),
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+            "solve": {"cycles": st["cycles"], "rel_residual": st["rel_residual"],
+                      "n_pairs": st["n_pairs"], "n_active_tiles": st["n_active_tiles"],
+                      "n_visible": st["n_visible"]},
+            "roofline": roofline, "kernels": kernels}
+
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        cores = os.cpu_count()
+        t0 = time.perf_counter()
+        ref, _, amb = O.render_view(scene, cam, mean, nthreads=cores)
+        tcpu = time.perf_counter() - t0
+        img = out.cpu().numpy().astype(np.float64)
+        err = float(np.abs(img - ref).max())
+        line["cpu_baseline"] = {"value": 1.0 / tcpu, "unit": "views/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"1 full view of {args.workload} (FP64 box-filtered "
+                                          "composite + DCT Neumann solve)"}
+        line["max_abs_err_vs_oracle"] = err
+        line["err_vs_oracle_range_scaled"] = err / max(1.0, float(ref.max() - ref.min()))
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+// Internal declarations shared by the CUDA translation units of libgdgs.
+// Not part of the ABI; include/gdgs.h is the public contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gdgs.h"
+
+namespace gdgs {
+
+constexpr int kTile = GDGS_TILE;        // raster tile edge (pixels)
+constexpr int kMaxCycles = 64;          // bound on V-cycles per solve
+constexpr int kMaxLevels = 24;          // bound on multigrid levels
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;         // keys per thread per radix block
+constexpr int kRadixBlock = kRadixThreads * kRadixItems;
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+
+// Device control block at offset 0 of every workspace. Zeroed at the start of
+// each call (except the fields after `persist_begin`, of which there are none:
+// the coarse-solver cache lives in its own region).
+struct Ctrl {
+  int status;          // first device error (atomicCAS from GDGS_OK)
+  int stopped;         // multigrid: convergence observed
+  int cycles;          // multigrid: V-cycles behind the returned iterate
+  int n_visible;       // Gaussians that survived projection
+  unsigned long long n_pairs;  // (tile, splat) pairs requested (uncapped)
+  unsigned n_active;   // tiles with at least one pair
+  unsigned pad0;
+  int max_cycles;
+  int channels;
+  double rtol;
+  double rnorm2[kMaxCycles + 1];             // ||rho - L u_k||^2, k = 0..
+  double sum_u[kMaxCycles + 1][GDGS_MAX_CHANNELS];  // sum of u_k per channel
+  double final_rnorm2;                       // residual of u when not stopped
+  double mean_set[GDGS_MAX_CHANNELS];
+};
+
+// Diagnostics hooks around every kernel launch (diag.cu).
+void diag_before(const char *name, cudaStream_t st);
+void diag_after(cudaStream_t st);
+struct LaunchScope {
+  cudaStream_t st;
+  LaunchScope(const char *name, cudaStream_t s) : st(s) { diag_before(name, s); }
+  ~LaunchScope() { diag_after(st); }
+};
+
+__device__ __forceinline__ void set_status(Ctrl *c, int code) {
+  atomicCAS(&c->status, GDGS_OK, code);
+}
+
+// Geometry of one multigrid level. Level l has ceil(N0 / 2^l) cells per side;
+// cell J covers fine pixels [J 2^l, min((J+1) 2^l, N0)), so only the last cell
+// of a side may be narrower. Widths are normalised by 2^l (full cell = 1).
+struct LevelGeom {
+  int H, W;            // cells
+  int shift;           // l
+  int H0, W0;          // finest grid
+  float lastx, lasty;  // normalised width of the last column / height of the last row
+  float ex, ey;        // 2 / (1 + lastx), 2 / (1 + lasty): face factors next to them
+  long long plane;     // floats per channel plane (H * W)
+};
+
+// ---------------------------------------------------------------- workspace plan
+struct Plan {
+  int64_t n;
+  int C, W, H;
+  int tiles_x, tiles_y, T;
+  unsigned pair_cap;
+  int radix_blocks_max;
+  // offsets in bytes from the workspace base
+  size_t off_ctrl;
+  size_t off_smean, off_sconic, off_rect;              // projected splats [n]
+  size_t off_dkey[2], off_dval[2];                     // depth sort [n]
+  size_t off_hist;                                     // radix histograms
+  size_t off_blocksum;                                 // scan partials
+  size_t off_pkey[2], off_pval[2];                     // pairs [pair_cap]
+  size_t off_range, off_active, off_mask;              // per tile
+  size_t off_maps;                                     // [C][2][H][W]
+  size_t off_rho, off_uhi, off_ulo, off_e0;            // level 0 [C][H][W]
+  size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1
+  size_t off_coarse;                                   // tag + FP64 inverse
+  int levels;         // number of levels (finest = 0, coarsest = levels-1)
+  int tail;           // first level solved inside one CTA per channel
+  int nc;             // unknowns on the coarsest level
+  LevelGeom lv[kMaxLevels];
+  size_t total;
+};
+
+bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
+               const gdgs_solver_opts &so, Plan *p);
+
+constexpr size_t kCoarseTagBytes = 256;
+struct CoarseTag {
+  unsigned long long magic;
+  int H0, W0, levels, Hc, Wc, nc;
+  int version;
+  int pad[5];
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaSuccess or the launch error; all enqueue on `st`.
+struct ProjectArgs {
+  const float *mean, *scale, *quat, *opacity, *grad;
+  int64_t n;
+  int C;
+  float w2c[12];
+  float fx, fy, cx, cy, znear;
+  int W, H, tiles_x, tiles_y;
+  float alpha_min, dilation, exp_coef;
+  // outputs (workspace)
+  float4 *smean;   // mx_hi, my_hi, mx_lo, my_lo
+  float4 *sconic;  // conic * exp_coef * log2(e) (a, 2b, c), opacity
+  uint32_t *key;   // float bits of the depth key, kInvalidKey when culled
+  uint2 *rect;     // x0 | x1 << 16, y0 | y1 << 16 (tiles, half open)
+  // optional outputs
+  float *o_mean2d, *o_cov2d, *o_depth;
+  int32_t *o_rect;
+  Ctrl *ctrl;
+};
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t st);
+
+// Stable LSD radix sort of 32-bit keys with 32-bit values over bits
+// [0, nbits). n = min(*n_dev, cap) if n_dev else cap. vals_in == nullptr means
+// the values are the element indices. Returns in *out_is_alt whether the
+// result sits in the alternate buffers.
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                             uint32_t *vals_alt, bool implicit_vals,
+                             const unsigned long long *n_dev, unsigned cap, int nbits,
+                             uint32_t *hist, int max_blocks, bool *out_is_alt,
+                             cudaStream_t st);
+
+struct BinArgs {
+  const uint32_t *order;   // Gaussian indices in depth order [n]
+  const uint2 *rect;
+  int64_t n;
+  int tiles_x, T;
+  unsigned pair_cap;
+  unsigned long long *blocksum;  // [ceil(n / kRadixBlock) + 1]
+  uint32_t *pkey, *pval;   // emitted pairs
+  Ctrl *ctrl;
+};
+cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st);
+
+cudaError_t launch_tile_ranges(const uint32_t *sorted_keys, Ctrl *ctrl, unsigned pair_cap,
+                               int T, uint2 *range, uint32_t *active, uint8_t *mask,
+                               cudaStream_t st);
+
+struct RasterArgs {
+  const float4 *smean, *sconic;
+  const float *grad;
+  const uint32_t *pval;     // Gaussian index of each sorted pair
+  const uint2 *range;       // [T]
+  const uint32_t *active;   // [T] active tile ids (when use_active)
+  int use_active;           // 1: only active tiles (count in ctrl->n_active)
+  int C, W, H, tiles_x, T;
+  float alpha_min, alpha_max, t_min;
+  float *maps;              // [C][2][H][W]
+  Ctrl *ctrl;
+};
+cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st);
+
+struct PoissonArgs {
+  const float *maps;        // [C][2][H][W]
+  const uint8_t *mask;      // [tiles_y][tiles_x] or null
+  int C, H, W, tiles_x;
+  float mean[GDGS_MAX_CHANNELS];
+  float *image;             // [C][H][W]
+  int nu1, nu2, max_cycles;
+  float rtol;
+  const Plan *plan;
+  char *ws;
+  Ctrl *ctrl;
+};
+cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st);
+
+}  // namespace gdgs

@@ -1,0 +1,916 @@
+// Poisson reconstruction of the image from its gradient maps (K6-K11).
+//
+// rho = div(g) (the Laplacian field is the divergence of the gradient field,
+// Sec. 1.5 "Sparsity"), then the Neumann problem L u = rho of Eq. p2d is solved
+// by multigrid, one of the linear-complexity solvers the paper lists (Sec. 2.1,
+// Sec. 2.2 "Poisson Equation"), and the free constant ("possible constant
+// difference", Sec. 2.1) is fixed by a supplied per-channel mean.
+//
+// Discretisation. L is the 5-point Neumann Laplacian on the pixel grid,
+// L u(i,j) = sum over in-grid neighbours n of (u_n - u_ij). Coarse level l has
+// ceil(N / 2^l) cells per side; cell J covers fine pixels [J 2^l, min((J+1) 2^l,
+// N)), so only a side's last cell can be narrow. Each level is the finite-volume
+// rediscretisation on its cells: face coefficient = face length / distance
+// between the two cell centres, right-hand side = sum of the children's
+// residuals. Transfers: restriction sums 2x2 children; prolongation is bilinear
+// in the cell-centre coordinates (constant beyond the outermost centres). The
+// coarsest grid (both sides <= coarse_max_dim) is solved directly in FP64 with a
+// dense inverse of -L + 11^T / n (SPD; its solution of a compatible system is the
+// zero-mean solution of L u = f), built once per grid shape by Gauss-Jordan on
+// the device and cached in the workspace under a tag.
+//
+// Smoother and blocking. Red-black Gauss-Seidel. On the large levels one CTA
+// owns a 32x64 output tile, loads it with a halo of 2 nu + 1 cells into shared
+// memory and runs all nu sweeps there (each half-sweep shrinks the valid region
+// by one cell), then fuses the residual with the 2x2 restriction (down) or the
+// prolongation with the post-sweeps (up). Levels that fit in shared memory are
+// handled by one CTA per channel that runs the rest of the V-cycle in place.
+//
+// Precision. An FP32 image carries a representation error that alone gives a
+// relative residual ~1e-5 on 1080p scenes, above the 1e-6 target. The finest
+// iterate is therefore kept as a float-float pair (hi + lo) and refined:
+// each cycle computes r = rho - L u in float-float arithmetic, runs the FP32
+// V-cycle on L e = r from e = 0, and adds e to u with an error-free sum. Every
+// coarser level works on FP32 corrections.
+//
+// Convergence is decided on the device: the finest "down" kernel of cycle k
+// accumulates ||rho - L u_k||^2; every later kernel of that cycle returns at
+// once when it is <= rtol^2 ||rho||^2, and the first one records the stop, so the
+// remaining launches of the cycle loop do no work.
+#include "gdgs_internal.cuh"
+
+namespace gdgs {
+
+namespace {
+
+constexpr int TY = 32, TX = 64;  // output tile of the shared-memory level kernels
+constexpr int kMgThreads = 256;
+constexpr int kTailThreads = 1024;
+
+// ------------------------------------------------------------------ operator
+
+__device__ __forceinline__ float wxf(const LevelGeom &g, int J) { return J == g.W - 1 ? g.lastx : 1.f; }
+__device__ __forceinline__ float wyf(const LevelGeom &g, int I) { return I == g.H - 1 ? g.lasty : 1.f; }
+
+struct Coef {
+  float e, w, s, n;
+};
+
+// Face coefficients of cell (I, J): face length / centre distance; 0 on the border.
+__device__ __forceinline__ Coef coef(const LevelGeom &g, int I, int J) {
+  const float wx = wxf(g, J), wy = wyf(g, I);
+  Coef c;
+  c.e = (J + 1 < g.W) ? wy * (J + 1 == g.W - 1 ? g.ex : 1.f) : 0.f;
+  c.w = (J > 0) ? wy * (J == g.W - 1 ? g.ex : 1.f) : 0.f;
+  c.s = (I + 1 < g.H) ? wx * (I + 1 == g.H - 1 ? g.ey : 1.f) : 0.f;
+  c.n = (I > 0) ? wx * (I == g.H - 1 ? g.ey : 1.f) : 0.f;
+  return c;
+}
+
+__device__ __forceinline__ bool interior(const LevelGeom &g, int I, int J) {
+  return I > 0 && J > 0 && I < g.H - 2 && J < g.W - 2;
+}
+
+__device__ __forceinline__ float gs_value(const LevelGeom &g, int I, int J, float uE, float uW,
+                                          float uS, float uN, float f) {
+  if (interior(g, I, J)) return 0.25f * ((uE + uW) + (uS + uN) - f);
+  const Coef c = coef(g, I, J);
+  const float d = c.e + c.w + c.s + c.n;
+  return d > 0.f ? (c.e * uE + c.w * uW + c.s * uS + c.n * uN - f) / d : 0.f;
+}
+
+__device__ __forceinline__ float residual(const LevelGeom &g, int I, int J, float u, float uE,
+                                          float uW, float uS, float uN, float f) {
+  if (interior(g, I, J)) return f - ((uE + uW) + (uS + uN) - 4.f * u);
+  const Coef c = coef(g, I, J);
+  return f - (c.e * (uE - u) + c.w * (uW - u) + c.s * (uS - u) + c.n * (uN - u));
+}
+
+// Error-free accumulation of e into the float-float pair (hi, lo).
+__device__ __forceinline__ void ds_add(float &hi, float &lo, float e) {
+  const float s = __fadd_rn(hi, e);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(e, bb));
+  const float l = __fadd_rn(lo, err);
+  const float h2 = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h2, s));
+  hi = h2;
+}
+
+struct P1 {
+  int i0, i1;
+  float w1;
+};
+
+// 1D bilinear weights for child index i of level `shift` from level shift+1
+// (nc cells), with n0 fine cells; centres are compared in doubled fine units.
+__device__ __forceinline__ P1 prolong1d(int i, int shift, int n0, int nc) {
+  const int cf = (i << shift) + min((i + 1) << shift, n0);
+  const int I0 = i >> 1;
+  const int C0 = (I0 << (shift + 1)) + min((I0 + 1) << (shift + 1), n0);
+  P1 p{I0, I0, 0.f};
+  if (cf != C0) {
+    const int I1 = cf < C0 ? I0 - 1 : I0 + 1;
+    if (I1 >= 0 && I1 < nc) {
+      const int C1 = (I1 << (shift + 1)) + min((I1 + 1) << (shift + 1), n0);
+      p.i1 = I1;
+      p.w1 = (float)abs(cf - C0) / (float)abs(C1 - C0);
+    }
+  }
+  return p;
+}
+
+__device__ __forceinline__ bool should_stop(Ctrl *ctrl, int k, int first) {
+  if (*(volatile int *)&ctrl->stopped) return true;
+  const double thr = ctrl->rtol * ctrl->rtol * ctrl->rnorm2[0];
+  if (ctrl->rnorm2[k] <= thr) {
+    if (first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+      ctrl->stopped = 1;
+      ctrl->cycles = k;
+    }
+    return true;
+  }
+  return false;
+}
+
+__device__ float block_sum(float v) {
+  __shared__ float part[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += part[i];
+  return s;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------ region helpers
+
+// One red-black half-sweep over the cells of colour `col` of a shared-memory
+// region (origin (ry0, rx0) in level coordinates, RY x RX cells), restricted to
+// cells at least `s` cells inside the region and inside the grid.
+template <int RY, int RX>
+__device__ __forceinline__ void half_sweep(float *U, const float *F, const LevelGeom &g, int ry0,
+                                           int rx0, int s, int col) {
+  const int y1 = RY - s, x1 = RX - s;
+  const int hw = (x1 - s + 1) >> 1;
+  const int cnt = (y1 - s) * hw;
+  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+    const int row = idx / hw;
+    const int m = idx - row * hw;
+    const int yy = s + row;
+    const int gy = ry0 + yy;
+    const int xx = s + (((gy + rx0 + s) ^ col) & 1) + 2 * m;
+    if (xx >= x1) continue;
+    const int gx = rx0 + xx;
+    if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
+    const int o = yy * RX + xx;
+    U[o] = gs_value(g, gy, gx, U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+  }
+}
+
+template <int RY, int RX>
+__device__ __forceinline__ void load_region(float *dst, const float *src, const LevelGeom &g,
+                                            int ry0, int rx0) {
+  for (int idx = threadIdx.x; idx < RY * RX; idx += blockDim.x) {
+    const int yy = idx / RX, xx = idx - yy * RX;
+    const int gy = ry0 + yy, gx = rx0 + xx;
+    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
+    dst[idx] = in ? src[(size_t)gy * g.W + gx] : 0.f;
+  }
+}
+
+// Residual of (U, F) on the children of each coarse cell of the output tile,
+// summed into the coarse right-hand side.
+template <int RY, int RX, int HALO>
+__device__ __forceinline__ void restrict_tile(const float *U, const float *F, const LevelGeom &g,
+                                              const LevelGeom &gc, int ty0, int tx0, float *fc) {
+  constexpr int CY = TY / 2, CX = TX / 2;
+  const int ry0 = ty0 - HALO, rx0 = tx0 - HALO;
+  for (int idx = threadIdx.x; idx < CY * CX; idx += blockDim.x) {
+    const int ci = idx / CX, cj = idx - ci * CX;
+    const int CI = (ty0 >> 1) + ci, CJ = (tx0 >> 1) + cj;
+    if (CI >= gc.H || CJ >= gc.W) continue;
+    float sum = 0.f;
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int gy = 2 * CI + di, gx = 2 * CJ + dj;
+        if (gy >= g.H || gx >= g.W) continue;
+        const int o = (gy - ry0) * RX + (gx - rx0);
+        sum += residual(g, gy, gx, U[o], U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+      }
+    fc[(size_t)CI * gc.W + CJ] = sum;
+  }
+}
+
+// Coarse region that covers the prolongation stencils of a fine region.
+struct CoarseBox {
+  int cy0, cx0, CRY, CRX;
+};
+
+__device__ __forceinline__ CoarseBox coarse_box(int ry0, int rx0, int RY, int RX) {
+  CoarseBox b;
+  b.cy0 = (ry0 >> 1) - 1;
+  b.cx0 = (rx0 >> 1) - 1;
+  b.CRY = ((ry0 + RY - 1) >> 1) + 1 - b.cy0 + 1;
+  b.CRX = ((rx0 + RX - 1) >> 1) + 1 - b.cx0 + 1;
+  return b;
+}
+
+__device__ __forceinline__ void load_coarse(float *EC, const float *uc, const LevelGeom &gc,
+                                            const CoarseBox &b) {
+  for (int idx = threadIdx.x; idx < b.CRY * b.CRX; idx += blockDim.x) {
+    const int yy = idx / b.CRX, xx = idx - yy * b.CRX;
+    const int gy = b.cy0 + yy, gx = b.cx0 + xx;
+    const bool in = gy >= 0 && gy < gc.H && gx >= 0 && gx < gc.W;
+    EC[idx] = in ? uc[(size_t)gy * gc.W + gx] : 0.f;
+  }
+}
+
+// U += P(EC) on every in-grid cell of the region.
+template <int RY, int RX>
+__device__ __forceinline__ void prolong_region(float *U, const float *EC, const LevelGeom &g,
+                                               const LevelGeom &gc, const CoarseBox &b, int ry0,
+                                               int rx0) {
+  for (int idx = threadIdx.x; idx < RY * RX; idx += blockDim.x) {
+    const int yy = idx / RX, xx = idx - yy * RX;
+    const int gy = ry0 + yy, gx = rx0 + xx;
+    if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
+    const P1 py = prolong1d(gy, g.shift, g.H0, gc.H);
+    const P1 px = prolong1d(gx, g.shift, g.W0, gc.W);
+    const float *r0 = EC + (py.i0 - b.cy0) * b.CRX;
+    const float *r1 = EC + (py.i1 - b.cy0) * b.CRX;
+    const int j0 = px.i0 - b.cx0, j1 = px.i1 - b.cx0;
+    const float a0 = r0[j0] + px.w1 * (r0[j1] - r0[j0]);
+    const float a1 = r1[j0] + px.w1 * (r1[j1] - r1[j0]);
+    U[idx] += a0 + py.w1 * (a1 - a0);
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+struct L0Args {
+  LevelGeom g0, g1;
+  const float *rho;
+  float *uhi, *ulo, *e0;
+  float *f1;        // level-1 right-hand side (down)
+  const float *u1;  // level-1 correction (up)
+};
+
+template <int NU>
+struct L0DownShape {
+  static constexpr int H = 2 * NU + 1;
+  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
+  static constexpr size_t smem = 4 * RN * sizeof(float);
+};
+
+// Finest level, first half of a cycle: r_k = rho - L u_k in float-float, its
+// norm, nu1 sweeps on L e = r_k from e = 0, then restriction of r_k - L e.
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg0_down_kernel(L0Args a, Ctrl *ctrl, int k) {
+  using S = L0DownShape<NU>;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
+  extern __shared__ float sm[];
+  float *R = sm, *E = sm + RN, *UH = sm + 2 * RN, *UL = sm + 3 * RN;
+  if (k > 0 && *(volatile int *)&ctrl->stopped) return;
+  const LevelGeom &g = a.g0;
+  const int c = blockIdx.z;
+  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+  const int ry0 = ty0 - H, rx0 = tx0 - H;
+  const size_t cb = (size_t)c * g.plane;
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
+    const int yy = idx / RX, xx = idx - yy * RX;
+    const int gy = ry0 + yy, gx = rx0 + xx;
+    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
+    const size_t o = cb + (size_t)gy * g.W + gx;
+    R[idx] = in ? a.rho[o] : 0.f;
+    E[idx] = 0.f;
+    if (k > 0) {
+      UH[idx] = in ? a.uhi[o] : 0.f;
+      UL[idx] = in ? a.ulo[o] : 0.f;
+    }
+  }
+  __syncthreads();
+  if (k > 0) {
+    for (int idx = threadIdx.x; idx < (RY - 2) * (RX - 2); idx += blockDim.x) {
+      const int yy = 1 + idx / (RX - 2), xx = 1 + idx % (RX - 2);
+      const int gy = ry0 + yy, gx = rx0 + xx;
+      if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
+      const int o = yy * RX + xx;
+      const float hi = UH[o], lo = UL[o];
+      float sh = 0.f, sl = 0.f;
+      if (gx + 1 < g.W) { sh += UH[o + 1] - hi; sl += UL[o + 1] - lo; }
+      if (gx > 0) { sh += UH[o - 1] - hi; sl += UL[o - 1] - lo; }
+      if (gy + 1 < g.H) { sh += UH[o + RX] - hi; sl += UL[o + RX] - lo; }
+      if (gy > 0) { sh += UH[o - RX] - hi; sl += UL[o - RX] - lo; }
+      R[o] = R[o] - (sh + sl);
+    }
+    __syncthreads();
+  }
+  // ||r_k||^2 over the output tile
+  float nrm = 0.f;
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ty = idx / TX, tx = idx - ty * TX;
+    const int gy = ty0 + ty, gx = tx0 + tx;
+    if (gy < g.H && gx < g.W) {
+      const float r = R[(ty + H) * RX + tx + H];
+      nrm = fmaf(r, r, nrm);
+    }
+  }
+  nrm = block_sum(nrm);
+  if (threadIdx.x == 0) atomicAdd(&ctrl->rnorm2[k], (double)nrm);
+  // pre-smoothing of the correction
+#pragma unroll
+  for (int s = 0; s < 2 * NU; ++s) {
+    half_sweep<RY, RX>(E, R, g, ry0, rx0, s + 1, s & 1);
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ty = idx / TX, tx = idx - ty * TX;
+    const int gy = ty0 + ty, gx = tx0 + tx;
+    if (gy < g.H && gx < g.W) a.e0[cb + (size_t)gy * g.W + gx] = E[(ty + H) * RX + tx + H];
+  }
+  restrict_tile<RY, RX, H>(E, R, g, a.g1, ty0, tx0, a.f1 + (size_t)c * a.g1.plane);
+}
+
+template <int NU>
+struct L0UpShape {
+  static constexpr int H = 2 * NU;
+  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
+  static constexpr int CRN = (RY / 2 + 4) * (RX / 2 + 4);
+  static constexpr size_t smem = (4 * RN + CRN) * sizeof(float);
+};
+
+// Finest level, second half: e += P e_1, nu2 sweeps on L e = r_k (r_k recomputed
+// from u_k and rho), u_{k+1} = u_k + e in float-float, and sum(u_{k+1}).
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg0_up_kernel(L0Args a, Ctrl *ctrl, int k) {
+  using S = L0UpShape<NU>;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
+  extern __shared__ float sm[];
+  float *R = sm, *E = sm + RN, *UH = sm + 2 * RN, *UL = sm + 3 * RN, *EC = sm + 4 * RN;
+  if (should_stop(ctrl, k, 0)) return;
+  const LevelGeom &g = a.g0;
+  const int c = blockIdx.z;
+  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+  const int ry0 = ty0 - H, rx0 = tx0 - H;
+  const size_t cb = (size_t)c * g.plane;
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
+    const int yy = idx / RX, xx = idx - yy * RX;
+    const int gy = ry0 + yy, gx = rx0 + xx;
+    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
+    const size_t o = cb + (size_t)gy * g.W + gx;
+    R[idx] = in ? a.rho[o] : 0.f;
+    E[idx] = in ? a.e0[o] : 0.f;
+    UH[idx] = (in && k > 0) ? a.uhi[o] : 0.f;
+    UL[idx] = (in && k > 0) ? a.ulo[o] : 0.f;
+  }
+  const CoarseBox b = coarse_box(ry0, rx0, RY, RX);
+  load_coarse(EC, a.u1 + (size_t)c * a.g1.plane, a.g1, b);
+  __syncthreads();
+  if (k > 0) {
+    for (int idx = threadIdx.x; idx < (RY - 2) * (RX - 2); idx += blockDim.x) {
+      const int yy = 1 + idx / (RX - 2), xx = 1 + idx % (RX - 2);
+      const int gy = ry0 + yy, gx = rx0 + xx;
+      if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
+      const int o = yy * RX + xx;
+      const float hi = UH[o], lo = UL[o];
+      float sh = 0.f, sl = 0.f;
+      if (gx + 1 < g.W) { sh += UH[o + 1] - hi; sl += UL[o + 1] - lo; }
+      if (gx > 0) { sh += UH[o - 1] - hi; sl += UL[o - 1] - lo; }
+      if (gy + 1 < g.H) { sh += UH[o + RX] - hi; sl += UL[o + RX] - lo; }
+      if (gy > 0) { sh += UH[o - RX] - hi; sl += UL[o - RX] - lo; }
+      R[o] = R[o] - (sh + sl);
+    }
+  }
+  prolong_region<RY, RX>(E, EC, g, a.g1, b, ry0, rx0);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2 * NU; ++s) {
+    half_sweep<RY, RX>(E, R, g, ry0, rx0, s + 1, s & 1);
+    __syncthreads();
+  }
+  float su = 0.f;
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ty = idx / TX, tx = idx - ty * TX;
+    const int gy = ty0 + ty, gx = tx0 + tx;
+    if (gy < g.H && gx < g.W) {
+      const int o = (ty + H) * RX + tx + H;
+      float hi = UH[o], lo = UL[o];
+      ds_add(hi, lo, E[o]);
+      const size_t go = cb + (size_t)gy * g.W + gx;
+      a.uhi[go] = hi;
+      a.ulo[go] = lo;
+      su += hi + lo;
+    }
+  }
+  su = block_sum(su);
+  if (threadIdx.x == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+}
+
+struct LvArgs {
+  LevelGeom g, gc;
+  float *f, *u;      // this level
+  float *fc;         // coarse right-hand side (down)
+  const float *uc;   // coarse correction (up)
+};
+
+template <int NU>
+struct LvDownShape {
+  static constexpr int H = 2 * NU + 1;
+  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
+  static constexpr size_t smem = 2 * RN * sizeof(float);
+};
+
+// Level l >= 1, down: nu1 sweeps from u = 0 and residual restriction.
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k, int first) {
+  using S = LvDownShape<NU>;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
+  extern __shared__ float sm[];
+  float *F = sm, *U = sm + RN;
+  if (should_stop(ctrl, k, first)) return;
+  const LevelGeom &g = a.g;
+  const int c = blockIdx.z;
+  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+  const int ry0 = ty0 - H, rx0 = tx0 - H;
+  load_region<RY, RX>(F, a.f + (size_t)c * g.plane, g, ry0, rx0);
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) U[idx] = 0.f;
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2 * NU; ++s) {
+    half_sweep<RY, RX>(U, F, g, ry0, rx0, s + 1, s & 1);
+    __syncthreads();
+  }
+  float *uo = a.u + (size_t)c * g.plane;
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ty = idx / TX, tx = idx - ty * TX;
+    const int gy = ty0 + ty, gx = tx0 + tx;
+    if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
+  }
+  restrict_tile<RY, RX, H>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
+}
+
+template <int NU>
+struct LvUpShape {
+  static constexpr int H = 2 * NU;
+  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
+  static constexpr int CRN = (RY / 2 + 4) * (RX / 2 + 4);
+  static constexpr size_t smem = (2 * RN + CRN) * sizeof(float);
+};
+
+// Level l >= 1, up: u += P u_{l+1}, nu2 sweeps.
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k) {
+  using S = LvUpShape<NU>;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
+  extern __shared__ float sm[];
+  float *F = sm, *U = sm + RN, *EC = sm + 2 * RN;
+  if (should_stop(ctrl, k, 0)) return;
+  const LevelGeom &g = a.g;
+  const int c = blockIdx.z;
+  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+  const int ry0 = ty0 - H, rx0 = tx0 - H;
+  load_region<RY, RX>(F, a.f + (size_t)c * g.plane, g, ry0, rx0);
+  load_region<RY, RX>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
+  const CoarseBox b = coarse_box(ry0, rx0, RY, RX);
+  load_coarse(EC, a.uc + (size_t)c * a.gc.plane, a.gc, b);
+  __syncthreads();
+  prolong_region<RY, RX>(U, EC, g, a.gc, b, ry0, rx0);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2 * NU; ++s) {
+    half_sweep<RY, RX>(U, F, g, ry0, rx0, s + 1, s & 1);
+    __syncthreads();
+  }
+  float *uo = a.u + (size_t)c * g.plane;
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ty = idx / TX, tx = idx - ty * TX;
+    const int gy = ty0 + ty, gx = tx0 + tx;
+    if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
+  }
+}
+
+// ------------------------------------------------------------------ tail (one CTA per channel)
+
+struct TailArgs {
+  int lt, L;
+  LevelGeom g[kMaxLevels];
+  int off[kMaxLevels];   // float offset of level l's (U, F) pair in shared memory
+  const float *f_lt;     // global rhs of level lt
+  float *u_lt;           // global correction of level lt (out)
+  const double *Minv;    // [nc][nc]
+  int nc;
+};
+
+__device__ __forceinline__ float tail_nb(const float *U, const LevelGeom &g, int I, int J) {
+  return (I >= 0 && I < g.H && J >= 0 && J < g.W) ? U[I * g.W + J] : 0.f;
+}
+
+__device__ void tail_half_sweep(float *U, const float *F, const LevelGeom &g, int col) {
+  const int hw = (g.W + 1) >> 1;
+  for (int idx = threadIdx.x; idx < g.H * hw; idx += blockDim.x) {
+    const int I = idx / hw, m = idx - I * hw;
+    const int J = ((I ^ col) & 1) + 2 * m;
+    if (J >= g.W) continue;
+    const int o = I * g.W + J;
+    U[o] = gs_value(g, I, J, tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
+                    tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[o]);
+  }
+}
+
+template <int NU1, int NU2>
+__global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k, int first) {
+  extern __shared__ float sm[];
+  if (should_stop(ctrl, k, first)) return;
+  const int c = blockIdx.x;
+  {
+    const LevelGeom &g = a.g[a.lt];
+    float *F = sm + a.off[a.lt] + g.H * g.W;
+    const float *src = a.f_lt + (size_t)c * g.plane;
+    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) F[i] = src[i];
+  }
+  __syncthreads();
+  for (int l = a.lt; l < a.L; ++l) {
+    const LevelGeom &g = a.g[l];
+    const LevelGeom &gc = a.g[l + 1];
+    float *U = sm + a.off[l], *F = U + g.H * g.W;
+    float *Fc = sm + a.off[l + 1] + gc.H * gc.W;
+    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) U[i] = 0.f;
+    __syncthreads();
+    for (int s = 0; s < 2 * NU1; ++s) {
+      tail_half_sweep(U, F, g, s & 1);
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < gc.H * gc.W; idx += blockDim.x) {
+      const int CI = idx / gc.W, CJ = idx - CI * gc.W;
+      float sum = 0.f;
+      for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj) {
+          const int I = 2 * CI + di, J = 2 * CJ + dj;
+          if (I >= g.H || J >= g.W) continue;
+          sum += residual(g, I, J, U[I * g.W + J], tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
+                          tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[I * g.W + J]);
+        }
+      Fc[idx] = sum;
+    }
+    __syncthreads();
+  }
+  {  // direct FP64 solve on the coarsest grid: u = Minv (-f)
+    const LevelGeom &g = a.g[a.L];
+    float *U = sm + a.off[a.L], *F = U + g.H * g.W;
+    for (int i = threadIdx.x; i < a.nc; i += blockDim.x) {
+      const double *row = a.Minv + (size_t)i * a.nc;
+      double acc = 0.0;
+      for (int j = 0; j < a.nc; ++j) acc = fma(row[j], -(double)F[j], acc);
+      U[i] = (float)acc;
+    }
+    __syncthreads();
+  }
+  for (int l = a.L - 1; l >= a.lt; --l) {
+    const LevelGeom &g = a.g[l];
+    const LevelGeom &gc = a.g[l + 1];
+    float *U = sm + a.off[l], *F = U + g.H * g.W;
+    const float *Uc = sm + a.off[l + 1];
+    for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
+      const int I = idx / g.W, J = idx - I * g.W;
+      const P1 py = prolong1d(I, g.shift, g.H0, gc.H);
+      const P1 px = prolong1d(J, g.shift, g.W0, gc.W);
+      const float *r0 = Uc + py.i0 * gc.W, *r1 = Uc + py.i1 * gc.W;
+      const float a0 = r0[px.i0] + px.w1 * (r0[px.i1] - r0[px.i0]);
+      const float a1 = r1[px.i0] + px.w1 * (r1[px.i1] - r1[px.i0]);
+      U[idx] += a0 + py.w1 * (a1 - a0);
+    }
+    __syncthreads();
+    for (int s = 0; s < 2 * NU2; ++s) {
+      tail_half_sweep(U, F, g, s & 1);
+      __syncthreads();
+    }
+  }
+  {
+    const LevelGeom &g = a.g[a.lt];
+    const float *U = sm + a.off[a.lt];
+    float *dst = a.u_lt + (size_t)c * g.plane;
+    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) dst[i] = U[i];
+  }
+}
+
+// ------------------------------------------------------------------ setup, divergence, finalize
+
+// Builds and inverts M = -L + 11^T / n of the coarsest grid in FP64 (SPD, so
+// Gauss-Jordan without pivoting is stable), unless the tag already matches.
+__global__ void __launch_bounds__(1024)
+coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
+  __shared__ int match;
+  __shared__ double fcol[260];
+  if (threadIdx.x == 0) {
+    const CoarseTag t = *tag;
+    match = t.magic == want.magic && t.H0 == want.H0 && t.W0 == want.W0 &&
+            t.levels == want.levels && t.Hc == want.Hc && t.Wc == want.Wc && t.nc == want.nc &&
+            t.version == want.version;
+  }
+  __syncthreads();
+  if (match) return;
+  const int n = g.H * g.W;
+  const double inv_n = 1.0 / n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    const int I = i / g.W, J = i - I * g.W;
+    const Coef cf = coef(g, I, J);
+    double v = inv_n;
+    if (j == i) v += (double)cf.e + cf.w + cf.s + cf.n;
+    else if (j == i + 1 && J + 1 < g.W) v -= cf.e;
+    else if (j == i - 1 && J > 0) v -= cf.w;
+    else if (j == i + g.W && I + 1 < g.H) v -= cf.s;
+    else if (j == i - g.W && I > 0) v -= cf.n;
+    A[idx] = v;
+  }
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    const double piv = A[(size_t)p * n + p];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fcol[i] = A[(size_t)i * n + p];
+    __syncthreads();
+    const double ip = 1.0 / piv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      A[(size_t)p * n + j] = (j == p ? 1.0 : A[(size_t)p * n + j]) * ip;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx - i * n;
+      if (i == p) continue;
+      const double cur = (j == p) ? 0.0 : A[idx];
+      A[idx] = cur - fcol[i] * A[(size_t)p * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    CoarseTag t = want;
+    t.magic = 0;
+    *tag = t;
+    __threadfence();
+    tag->magic = want.magic;
+  }
+}
+
+struct DivArgs {
+  const float *maps;
+  const uint8_t *mask;
+  int C, H, W, tiles_x;
+  float *rho;
+  float rtol;
+  int max_cycles;
+};
+
+__device__ __forceinline__ bool tile_on(const uint8_t *mask, int tiles_x, int i, int j) {
+  return !mask || mask[(i / kTile) * tiles_x + (j / kTile)];
+}
+
+// rho(i,j) = [j<W-1] gx(i,j) - [j>=1] gx(i,j-1) + [i<H-1] gy(i,j) - [i>=1] gy(i-1,j),
+// with gradients of tiles whose mask is 0 read as zero.
+__global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    ctrl->rtol = a.rtol;
+    ctrl->max_cycles = a.max_cycles;
+    ctrl->channels = a.C;
+  }
+  const int c = blockIdx.y;
+  const size_t plane = (size_t)a.H * a.W;
+  const float *gxp = a.maps + (size_t)(2 * c) * plane;
+  const float *gyp = gxp + plane;
+  bool bad = false;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p / a.W), j = (int)(p - (size_t)i * a.W);
+    float r = 0.f;
+    if (j + 1 < a.W && tile_on(a.mask, a.tiles_x, i, j)) r += gxp[p];
+    if (j >= 1 && tile_on(a.mask, a.tiles_x, i, j - 1)) r -= gxp[p - 1];
+    if (i + 1 < a.H && tile_on(a.mask, a.tiles_x, i, j)) r += gyp[p];
+    if (i >= 1 && tile_on(a.mask, a.tiles_x, i - 1, j)) r -= gyp[p - a.W];
+    bad |= !isfinite(r);
+    a.rho[(size_t)c * plane + p] = r;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(ctrl, GDGS_ERR_NONFINITE);
+}
+
+struct FinArgs {
+  LevelGeom g0;
+  const float *rho, *uhi, *ulo;
+  float *image;
+  float mean[GDGS_MAX_CHANNELS];
+};
+
+// image = u + (m_c - mean(u_c)); the residual of u when the loop ran out of cycles.
+__global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
+  const int stopped = ctrl->stopped;
+  const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
+  const int c = blockIdx.y;
+  const LevelGeom &g = a.g0;
+  const size_t plane = (size_t)g.H * g.W;
+  const double npx = (double)plane;
+  const float shift = (float)((double)a.mean[c] - ctrl->sum_u[kf][c] / npx);
+  const size_t cb = (size_t)c * plane;
+  float r2 = 0.f;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const float hi = kf > 0 ? a.uhi[cb + p] : 0.f;
+    const float lo = kf > 0 ? a.ulo[cb + p] : 0.f;
+    a.image[cb + p] = hi + (lo + shift);
+    if (!stopped && kf > 0) {
+      const int i = (int)(p / g.W), j = (int)(p - (size_t)i * g.W);
+      float sh = 0.f, sl = 0.f;
+      if (j + 1 < g.W) { sh += a.uhi[cb + p + 1] - hi; sl += a.ulo[cb + p + 1] - lo; }
+      if (j > 0) { sh += a.uhi[cb + p - 1] - hi; sl += a.ulo[cb + p - 1] - lo; }
+      if (i + 1 < g.H) { sh += a.uhi[cb + p + g.W] - hi; sl += a.ulo[cb + p + g.W] - lo; }
+      if (i > 0) { sh += a.uhi[cb + p - g.W] - hi; sl += a.ulo[cb + p - g.W] - lo; }
+      const float r = a.rho[cb + p] - (sh + sl);
+      r2 = fmaf(r, r, r2);
+    }
+  }
+  if (!stopped && kf > 0) {
+    r2 = block_sum(r2);
+    if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->mean_set[c] = a.mean[c];
+    if (c == 0 && !stopped) ctrl->cycles = kf;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NU>
+cudaError_t launch_mg0_down(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  const size_t sm = L0DownShape<NU>::smem;
+  cudaError_t e = set_smem(mg0_down_kernel<NU>, sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
+  { LaunchScope ls_("mg0_down", st); mg0_down_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t launch_mg0_up(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  const size_t sm = L0UpShape<NU>::smem;
+  cudaError_t e = set_smem(mg0_up_kernel<NU>, sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
+  { LaunchScope ls_("mg0_up", st); mg0_up_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t launch_mg_down(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
+  const size_t sm = LvDownShape<NU>::smem;
+  cudaError_t e = set_smem(mg_down_kernel<NU>, sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
+  { LaunchScope ls_("mg_down", st); mg_down_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k, first); }
+  return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  const size_t sm = LvUpShape<NU>::smem;
+  cudaError_t e = set_smem(mg_up_kernel<NU>, sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
+  { LaunchScope ls_("mg_up", st); mg_up_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  return cudaGetLastError();
+}
+
+template <int NU1, int NU2>
+cudaError_t launch_tail_t(const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int first, int C,
+                          cudaStream_t st) {
+  cudaError_t e = set_smem(mg_tail_kernel<NU1, NU2>, sm);
+  if (e != cudaSuccess) return e;
+  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, kTailThreads, sm, st>>>(a, ctrl, k, first); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tail(int nu1, int nu2, const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int first,
+                        int C, cudaStream_t st) {
+#define GDGS_TAIL(A, B) \
+  if (nu1 == A && nu2 == B) return launch_tail_t<A, B>(a, sm, ctrl, k, first, C, st);
+  GDGS_TAIL(1, 1) GDGS_TAIL(1, 2) GDGS_TAIL(1, 3)
+  GDGS_TAIL(2, 1) GDGS_TAIL(2, 2) GDGS_TAIL(2, 3)
+  GDGS_TAIL(3, 1) GDGS_TAIL(3, 2) GDGS_TAIL(3, 3)
+#undef GDGS_TAIL
+  return cudaErrorInvalidValue;
+}
+
+#define GDGS_NU_DISPATCH(NU, CALL) \
+  ((NU) == 1 ? CALL<1> : (NU) == 2 ? CALL<2> : CALL<3>)
+
+}  // namespace
+
+cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
+  const Plan &p = *a.plan;
+  char *ws = a.ws;
+  Ctrl *ctrl = a.ctrl;
+  float *rho = (float *)(ws + p.off_rho);
+  float *uhi = (float *)(ws + p.off_uhi);
+  float *ulo = (float *)(ws + p.off_ulo);
+  float *e0 = (float *)(ws + p.off_e0);
+  cudaError_t e;
+
+  DivArgs d{a.maps, a.mask, a.C, a.H, a.W, a.tiles_x, rho, a.rtol, a.max_cycles};
+  {
+    const size_t plane = (size_t)a.H * a.W;
+    int bx = (int)((plane + 255) / 256);
+    if (bx > 4096) bx = 4096;
+    { LaunchScope ls_("divergence", st); divergence_kernel<<<dim3(bx, a.C), 256, 0, st>>>(d, ctrl); }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+
+  // coarse factor (cached in the workspace)
+  const LevelGeom &gcoarse = p.lv[p.levels - 1];
+  CoarseTag want{};
+  want.magic = 0x4744475343303031ull;  // "GDGSC001"
+  want.H0 = a.H;
+  want.W0 = a.W;
+  want.levels = p.levels;
+  want.Hc = gcoarse.H;
+  want.Wc = gcoarse.W;
+  want.nc = p.nc;
+  want.version = 1;
+  CoarseTag *tag = (CoarseTag *)(ws + p.off_coarse);
+  double *Minv = (double *)(ws + p.off_coarse + kCoarseTagBytes);
+  { LaunchScope ls_("coarse_setup", st); coarse_setup_kernel<<<1, 1024, 0, st>>>(gcoarse, Minv, tag, want); }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  L0Args l0{p.lv[0], p.lv[1], rho, uhi, ulo, e0, (float *)(ws + p.off_lf[1]),
+            (const float *)(ws + p.off_lu[1])};
+  TailArgs ta{};
+  ta.lt = p.tail;
+  ta.L = p.levels - 1;
+  int off = 0;
+  for (int l = 0; l < p.levels; ++l) {
+    ta.g[l] = p.lv[l];
+    if (l >= p.tail) {
+      ta.off[l] = off;
+      off += 2 * p.lv[l].H * p.lv[l].W;
+    }
+  }
+  const size_t tail_smem = (size_t)off * sizeof(float);
+  ta.f_lt = (const float *)(ws + p.off_lf[p.tail]);
+  ta.u_lt = (float *)(ws + p.off_lu[p.tail]);
+  ta.Minv = Minv;
+  ta.nc = p.nc;
+
+  for (int k = 0; k < a.max_cycles; ++k) {
+    e = a.nu1 == 1 ? launch_mg0_down<1>(l0, ctrl, k, a.C, st)
+        : a.nu1 == 2 ? launch_mg0_down<2>(l0, ctrl, k, a.C, st)
+                     : launch_mg0_down<3>(l0, ctrl, k, a.C, st);
+    if (e != cudaSuccess) return e;
+    for (int l = 1; l < p.tail; ++l) {
+      LvArgs la{p.lv[l], p.lv[l + 1], (float *)(ws + p.off_lf[l]), (float *)(ws + p.off_lu[l]),
+                (float *)(ws + p.off_lf[l + 1]), (const float *)(ws + p.off_lu[l + 1])};
+      const int first = (l == 1);
+      e = a.nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, a.C, st)
+          : a.nu1 == 2 ? launch_mg_down<2>(la, ctrl, k, first, a.C, st)
+                       : launch_mg_down<3>(la, ctrl, k, first, a.C, st);
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_tail(a.nu1, a.nu2, ta, tail_smem, ctrl, k, p.tail == 1 ? 1 : 0, a.C, st);
+    if (e != cudaSuccess) return e;
+    for (int l = p.tail - 1; l >= 1; --l) {
+      LvArgs la{p.lv[l], p.lv[l + 1], (float *)(ws + p.off_lf[l]), (float *)(ws + p.off_lu[l]),
+                (float *)(ws + p.off_lf[l + 1]), (const float *)(ws + p.off_lu[l + 1])};
+      e = a.nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, a.C, st)
+          : a.nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, a.C, st)
+                       : launch_mg_up<3>(la, ctrl, k, a.C, st);
+      if (e != cudaSuccess) return e;
+    }
+    e = a.nu2 == 1 ? launch_mg0_up<1>(l0, ctrl, k, a.C, st)
+        : a.nu2 == 2 ? launch_mg0_up<2>(l0, ctrl, k, a.C, st)
+                     : launch_mg0_up<3>(l0, ctrl, k, a.C, st);
+    if (e != cudaSuccess) return e;
+  }
+
+  FinArgs fa{};
+  fa.g0 = p.lv[0];
+  fa.rho = rho;
+  fa.uhi = uhi;
+  fa.ulo = ulo;
+  fa.image = a.image;
+  for (int c = 0; c < GDGS_MAX_CHANNELS; ++c) fa.mean[c] = a.mean[c];
+  {
+    const size_t plane = (size_t)a.H * a.W;
+    int bx = (int)((plane + 255) / 256);
+    if (bx > 2048) bx = 2048;
+    { LaunchScope ls_("finalize", st); finalize_kernel<<<dim3(bx, a.C), 256, 0, st>>>(fa, ctrl); }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gdgs

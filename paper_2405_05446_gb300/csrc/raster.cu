@@ -1,0 +1,113 @@
+// Tile rasteriser of the gradient attribute (K5).
+//
+// One CTA of 256 threads per non-empty 16x16 tile, one pixel per thread. The
+// tile's splats are already in front-to-back order (sort.cu); they are staged in
+// batches of 256 into shared memory and every pixel composites them as in
+// Eq. gdgs2d (Eq. color with the gradient attribute):
+//   G = exp(-k d^T conic d), a = min(alpha_max, alpha G), skip a < alpha_min,
+//   acc += g a T, T *= (1 - a), stop once T < t_min.
+// Tiles no splat reaches are never launched (the field is sparse, Sec. 2.2).
+//
+// The splat centre is staged relative to the tile origin from its (hi, lo) pair,
+// so the per-pixel offset d keeps FP32 relative precision anywhere in the image.
+// exp is evaluated as ex2.approx on -k log2(e) d^T conic d (the factor is folded
+// into the conic at projection); splats whose exponent already puts them below
+// alpha_min (with a 1e-3 margin in the exponent) are skipped without the exp.
+#include "gdgs_internal.cuh"
+
+namespace gdgs {
+
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
+  constexpr int Q = 2 * C;
+  __shared__ float s_mx[256], s_my[256], s_ca[256], s_cb[256], s_cc[256], s_opa[256], s_lim[256];
+  __shared__ float s_g[Q][256];
+  const unsigned ntiles = a.use_active ? a.ctrl->n_active : (unsigned)a.T;
+  if (blockIdx.x >= ntiles) return;
+  const int tile = a.use_active ? (int)a.active[blockIdx.x] : (int)blockIdx.x;
+  const int tyi = tile / a.tiles_x, txi = tile - tyi * a.tiles_x;
+  const int x0 = txi * kTile, y0 = tyi * kTile;
+  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int px = x0 + lx, py = y0 + ly;
+  const bool inside = px < a.W && py < a.H;
+  const float fpx = lx + 0.5f, fpy = ly + 0.5f;
+  const float x0f = (float)x0, y0f = (float)y0;
+  const uint2 rg = a.range[tile];
+  const float amin = a.alpha_min, amax = a.alpha_max, tmin = a.t_min;
+
+  float acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = 0.f;
+  float T = 1.f;
+  bool done = !inside;
+
+  for (unsigned s = rg.x; s < rg.y; s += 256) {
+    if (__syncthreads_and(done)) break;
+    const unsigned j = s + threadIdx.x;
+    if (j < rg.y) {
+      const uint32_t g = a.pval[j];
+      const float4 m = a.smean[g];
+      const float4 k = a.sconic[g];
+      s_mx[threadIdx.x] = (m.x - x0f) + m.z;
+      s_my[threadIdx.x] = (m.y - y0f) + m.w;
+      s_ca[threadIdx.x] = k.x;
+      s_cb[threadIdx.x] = k.y;
+      s_cc[threadIdx.x] = k.z;
+      s_opa[threadIdx.x] = k.w;
+      s_lim[threadIdx.x] = log2f(k.w / amin) + 1e-3f;
+      const float *gp = a.grad + (size_t)g * Q;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s_g[q][threadIdx.x] = gp[q];
+    }
+    __syncthreads();
+    const int cnt = min(256u, rg.y - s);
+    if (!done) {
+      for (int k = 0; k < cnt; ++k) {
+        const float dx = fpx - s_mx[k], dy = fpy - s_my[k];
+        const float p2 = dx * fmaf(s_ca[k], dx, s_cb[k] * dy) + s_cc[k] * dy * dy;
+        if (p2 > s_lim[k]) continue;
+        const float al = fminf(amax, s_opa[k] * ex2_approx(-p2));
+        if (al < amin) continue;
+        const float w = al * T;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] = fmaf(s_g[q][k], w, acc[q]);
+        T = T * (1.f - al);
+        if (T < tmin) {
+          done = true;
+          break;
+        }
+      }
+    }
+  }
+  if (inside) {
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t o = (size_t)py * a.W + px;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a.maps[q * plane + o] = acc[q];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st) {
+  if (a.T == 0) return cudaSuccess;
+  LaunchScope ls_("raster", st);
+  switch (a.C) {
+    case 1: raster_kernel<1><<<a.T, 256, 0, st>>>(a); break;
+    case 2: raster_kernel<2><<<a.T, 256, 0, st>>>(a); break;
+    case 3: raster_kernel<3><<<a.T, 256, 0, st>>>(a); break;
+    case 4: raster_kernel<4><<<a.T, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gdgs

@@ -1,0 +1,330 @@
+// Binning of splats into 16x16 tiles in front-to-back order (K2-K4).
+//
+// The composite of Eq. color / Eq. gdgs2d visits splats "sorted from the view
+// direction". The path orders them in two stable sorts instead of one wide key:
+//   1. sort the Gaussians by their FP32 depth key (32-bit keys, N items);
+//   2. walk them in that order, emit one (tile, Gaussian) pair per touched tile,
+//      so pairs come out depth-ordered;
+//   3. stable-sort the pairs by tile id only (ceil(log2 T) bits, 2 passes at
+//      1080p). Stability keeps depth order inside each tile, ties by index.
+// Compared with a 64-bit (tile | depth) key this sorts 13 instead of 45 bits per
+// pair and moves 8 instead of 12 bytes per pair and pass.
+//
+// The radix sort is a classic three-kernel LSD pass (block histograms, one scan
+// over digit-major histograms, stable scatter). Ranking inside a block is
+// stable: items are taken in rounds of 256 consecutive keys; within a warp peers
+// of a digit are found with __match_any_sync and ranked by lane; warps are
+// ranked in order through a shared-memory prefix per digit.
+#include "gdgs_internal.cuh"
+
+namespace gdgs {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned item_count(const unsigned long long *n_dev, unsigned cap) {
+  if (!n_dev) return cap;
+  const unsigned long long n = *n_dev;
+  return n < cap ? (unsigned)n : cap;
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+radix_hist_kernel(const uint32_t *keys, const unsigned long long *n_dev, unsigned cap,
+                  int shift, unsigned mask, uint32_t *hist) {
+  __shared__ unsigned sh[256];
+  const unsigned n = item_count(n_dev, cap);
+  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  if (blockIdx.x >= nb) return;
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned base = blockIdx.x * kRadixBlock;
+#pragma unroll 4
+  for (int r = 0; r < kRadixItems; ++r) {
+    const unsigned i = base + r * kRadixThreads + threadIdx.x;
+    if (i < n) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x <= mask) hist[threadIdx.x * nb + blockIdx.x] = sh[threadIdx.x];
+}
+
+// Exclusive scan of the digit-major histogram (length (mask+1) * nb) in place.
+__global__ void __launch_bounds__(1024)
+radix_scan_kernel(uint32_t *hist, const unsigned long long *n_dev, unsigned cap, unsigned mask) {
+  __shared__ unsigned warp_tot[32];
+  const unsigned n = item_count(n_dev, cap);
+  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  const unsigned m = (mask + 1) * nb;
+  const unsigned per = (m + blockDim.x - 1) / blockDim.x;
+  const unsigned b = threadIdx.x * per, e = min(b + per, m);
+  unsigned s = 0;
+  for (unsigned i = b; i < e; ++i) s += hist[i];
+  // block exclusive scan of s
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  unsigned run = x - s + (w > 0 ? warp_tot[w - 1] : 0u);
+  for (unsigned i = b; i < e; ++i) {
+    const unsigned v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
+                     uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
+                     unsigned mask, const uint32_t *hist) {
+  constexpr int kWarps = kRadixThreads / 32;
+  __shared__ unsigned run[256];
+  __shared__ unsigned wcnt[kWarps][256];
+  const unsigned n = item_count(n_dev, cap);
+  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  if (blockIdx.x >= nb) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x <= mask) run[threadIdx.x] = hist[threadIdx.x * nb + blockIdx.x];
+  const unsigned base = blockIdx.x * kRadixBlock;
+  for (int r = 0; r < kRadixItems; ++r) {
+    const unsigned i = base + r * kRadixThreads + threadIdx.x;
+    if (base + r * kRadixThreads >= n) break;  // uniform across the block
+    const bool valid = i < n;
+    const uint32_t key = valid ? keys_in[i] : 0u;
+    const uint32_t val = valid ? (vals_in ? vals_in[i] : i) : 0u;
+    const unsigned d = valid ? ((key >> shift) & mask) : 0x1000u;
+    for (int t = threadIdx.x; t < kWarps * 256; t += kRadixThreads) (&wcnt[0][0])[t] = 0u;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x <= mask) {
+      unsigned b2 = run[threadIdx.x];
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) {
+        const unsigned c = wcnt[k][threadIdx.x];
+        wcnt[k][threadIdx.x] = b2;
+        b2 += c;
+      }
+      run[threadIdx.x] = b2;
+    }
+    __syncthreads();
+    if (valid) {
+      const unsigned pos = wcnt[w][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pair emission
+
+__device__ __forceinline__ unsigned rect_tiles(uint2 r) {
+  const unsigned x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu, y1 = r.y >> 16;
+  return (x1 - x0) * (y1 - y0);
+}
+
+// Block-wide exclusive scan of 64-bit values for 256 threads.
+__device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long *total) {
+  __shared__ unsigned long long wt[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  unsigned long long before = 0, all = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < w) before += wt[k];
+    all += wt[k];
+  }
+  __syncthreads();
+  *total = all;
+  return x - v + before;
+}
+
+// Sum of tile counts per block of kRadixBlock depth-ordered Gaussians.
+__global__ void __launch_bounds__(256) count_kernel(BinArgs a) {
+  const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+  unsigned long long s = 0;
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = base + r * 256 + threadIdx.x;
+    if (i < a.n) s += rect_tiles(a.rect[a.order[i]]);
+  }
+  unsigned long long tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) a.blocksum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) blocksum_scan_kernel(BinArgs a, int nb) {
+  __shared__ unsigned long long wt[32];
+  const int per = (nb + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(b + per, nb);
+  unsigned long long s = 0;
+  for (int i = b; i < e; ++i) s += a.blocksum[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = wt[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    wt[lane] = t;
+  }
+  __syncthreads();
+  unsigned long long run = x - s + (w > 0 ? wt[w - 1] : 0ull);
+  for (int i = b; i < e; ++i) {
+    const unsigned long long v = a.blocksum[i];
+    a.blocksum[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 1023) {
+    const unsigned long long total = wt[31];
+    a.ctrl->n_pairs = total;
+    if (total > a.pair_cap) set_status(a.ctrl, GDGS_ERR_CAPACITY);
+  }
+}
+
+__global__ void __launch_bounds__(256) emit_kernel(BinArgs a) {
+  const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+  unsigned long long off = a.blocksum[blockIdx.x];
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = base + r * 256 + threadIdx.x;
+    const bool in = i < a.n;
+    uint32_t g = 0;
+    uint2 rc = make_uint2(0, 0);
+    if (in) {
+      g = a.order[i];
+      rc = a.rect[g];
+    }
+    const unsigned cnt = in ? rect_tiles(rc) : 0u;
+    unsigned long long tot;
+    const unsigned long long my = off + block_exclusive_scan(cnt, &tot);
+    if (cnt) {
+      const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
+      unsigned long long p = my;
+      for (unsigned ty = y0; ty < y1; ++ty)
+        for (unsigned tx = x0; tx < x1; ++tx, ++p)
+          if (p < a.pair_cap) {
+            a.pkey[p] = ty * (unsigned)a.tiles_x + tx;
+            a.pval[p] = g;
+          }
+    }
+    off += tot;
+  }
+}
+
+// Tile ranges by binary search in the tile-sorted keys; compaction of the
+// non-empty tiles into `active` (order irrelevant: tiles are independent).
+__global__ void __launch_bounds__(256)
+ranges_kernel(const uint32_t *keys, Ctrl *ctrl, unsigned cap, int T, uint2 *range,
+              uint32_t *active, uint8_t *mask) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long np = ctrl->n_pairs;
+  const unsigned n = np < cap ? (unsigned)np : cap;
+  bool act = false;
+  if (t < T) {
+    unsigned lo = 0, hi = n;
+    while (lo < hi) {  // first index with key >= t
+      const unsigned mid = (lo + hi) >> 1;
+      if (keys[mid] < (unsigned)t) lo = mid + 1; else hi = mid;
+    }
+    const unsigned s = lo;
+    hi = n;
+    while (lo < hi) {  // first index with key > t
+      const unsigned mid = (lo + hi) >> 1;
+      if (keys[mid] <= (unsigned)t) lo = mid + 1; else hi = mid;
+    }
+    range[t] = make_uint2(s, lo);
+    act = lo > s;
+    mask[t] = act ? 1 : 0;
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, act);
+  unsigned base = 0;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0 && ball) base = atomicAdd(&ctrl->n_active, __popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (act) active[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)t;
+}
+
+}  // namespace
+
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                             uint32_t *vals_alt, bool implicit_vals,
+                             const unsigned long long *n_dev, unsigned cap, int nbits,
+                             uint32_t *hist, int max_blocks, bool *out_is_alt,
+                             cudaStream_t st) {
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  bool alt = false;
+  bool first = true;
+  const unsigned blocks = (unsigned)max_blocks;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    const int bits = nbits - shift < 8 ? nbits - shift : 8;
+    const unsigned mask = (1u << bits) - 1u;
+    if (blocks == 0) break;
+    { LaunchScope ls_("radix_hist", st); radix_hist_kernel<<<blocks, kRadixThreads, 0, st>>>(ki, n_dev, cap, shift, mask, hist); }
+    { LaunchScope ls_("radix_scan", st); radix_scan_kernel<<<1, 1024, 0, st>>>(hist, n_dev, cap, mask); }
+    {
+      LaunchScope ls_("radix_scatter", st);
+      radix_scatter_kernel<<<blocks, kRadixThreads, 0, st>>>(
+          ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist);
+    }
+    first = false;
+    uint32_t *t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    alt = !alt;
+  }
+  *out_is_alt = alt;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  const int nb = (int)((a.n + kRadixBlock - 1) / kRadixBlock);
+  { LaunchScope ls_("pair_count", st); count_kernel<<<nb, 256, 0, st>>>(a); }
+  { LaunchScope ls_("pair_scan", st); blocksum_scan_kernel<<<1, 1024, 0, st>>>(a, nb); }
+  { LaunchScope ls_("pair_emit", st); emit_kernel<<<nb, 256, 0, st>>>(a); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const uint32_t *sorted_keys, Ctrl *ctrl, unsigned pair_cap,
+                               int T, uint2 *range, uint32_t *active, uint8_t *mask,
+                               cudaStream_t st) {
+  { LaunchScope ls_("tile_ranges", st); ranges_kernel<<<(T + 255) / 256, 256, 0, st>>>(sorted_keys, ctrl, pair_cap, T, range, active, mask); }
+  return cudaGetLastError();
+}
+
+}  // namespace gdgs

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2405_05446_gb300 as G
+from paper_2405_05446_gb300 import scenes as S
+
+from gpu_util import (AMB_FRAC_MAX, IMG_TOL, MAP_TOL, ensure_lib, gpu_maps, gpu_poisson,
+                      img_err, map_rel_err, oracle_opts)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def _small_prims(n=20000, w=330, h=190, seed=0, channels=3):
+    cam = S.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), w, h)
+    return S.primitives_scene(seed, n=n, orient_camera=cam, channels=channels), cam
+
+
+# ------------------------------------------------------------------ projection
+
+def test_projection_matches_oracle():
+    scene = S.tiny_scene(3, n=2000)
+    cam = S.look_at_camera((0.7, -0.4, -2.8), (0.1, 0.0, 0.2), 96, 72, hfov_deg=55)
+    ro = G.raster_opts()
+    g = G.gaussians_to_device(scene)
+    ws = torch.empty(G.workspace_size(scene.n, 3, cam.width, cam.height, ro, None), dtype=torch.uint8, device="cuda")
+    m2 = torch.zeros((scene.n, 2), device="cuda")
+    cv = torch.zeros((scene.n, 3), device="cuda")
+    dp = torch.zeros(scene.n, device="cuda")
+    rc = torch.zeros((scene.n, 4), dtype=torch.int32, device="cuda")
+    G.project(g, cam, ws, ro, m2, cv, dp, rc)
+    st = G.sync_status(ws)
+    assert st["status"] == 0
+    proj = O.project(scene, cam, oracle_opts(ro))
+    vis = rc[:, 2].cpu().numpy() > rc[:, 0].cpu().numpy()
+    # the depth key decides the order: identical bits on both sides
+    ok = proj[:, O.VALID] > 0
+    np.testing.assert_array_equal(dp.cpu().numpy()[vis], proj[vis, O.KEY].astype(np.float32))
+    assert not np.any(vis & ~ok)
+    m2 = m2.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(m2[vis, 0], proj[vis, O.MX], atol=1e-4, rtol=0)
+    np.testing.assert_allclose(m2[vis, 1], proj[vis, O.MY], atol=1e-4, rtol=0)
+    cv = cv.cpu().numpy().astype(np.float64)
+    for k, col in enumerate([O.S00, O.S01, O.S11]):
+        scale = np.maximum(proj[vis, O.S00], proj[vis, O.S11])
+        assert np.max(np.abs(cv[vis, k] - proj[vis, col]) / scale) < 1e-5
+    # the tile rectangle covers every pixel of the exact footprint box
+    rc = rc.cpu().numpy()
+    W, H = cam.width, cam.height
+    for i in np.nonzero(ok)[0]:
+        j0 = int(np.ceil(proj[i, O.XMIN] - 0.5)); j1 = int(np.floor(proj[i, O.XMAX] - 0.5))
+        i0 = int(np.ceil(proj[i, O.YMIN] - 0.5)); i1 = int(np.floor(proj[i, O.YMAX] - 0.5))
+        j0, j1, i0, i1 = max(j0, 0), min(j1, W - 1), max(i0, 0), min(i1, H - 1)
+        if j0 > j1 or i0 > i1:
+            continue
+        assert rc[i, 0] <= j0 // 16 and rc[i, 2] > j1 // 16, i
+        assert rc[i, 1] <= i0 // 16 and rc[i, 3] > i1 // 16, i
+    assert st["n_visible"] == int(vis.sum())
+
+
+# ------------------------------------------------------------------ rasteriser
+
+@pytest.mark.parametrize("channels", [3, 1, 4])
+def test_gradient_maps_tiny(channels):
+    scene = S.tiny_scene(0, channels=channels)
+    cam = S.tiny_camera()
+    gm, _, st = gpu_maps(scene, cam)
+    assert st["status"] == 0
+    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    assert amb.mean() <= AMB_FRAC_MAX
+    assert map_rel_err(gm, om, amb) <= MAP_TOL
+
+
+def test_gradient_maps_ragged_prims_several_tiles():
+    scene, cam = _small_prims()
+    gm, _, st = gpu_maps(scene, cam)
+    assert st["status"] == 0 and st["n_pairs"] > 0
+    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    assert amb.mean() <= AMB_FRAC_MAX
+    assert map_rel_err(gm, om, amb) <= MAP_TOL
+
+
+def test_gradient_maps_half_exponent_option():
+    scene = S.tiny_scene(5, n=500)
+    cam = S.tiny_camera(80, 48)
+    ro = G.raster_opts(exp_coef=0.5, dilation=0.1)
+    gm, _, st = gpu_maps(scene, cam, ro)
+    om, amb = O.render_gradients(scene, cam, oracle_opts(ro))
+    assert map_rel_err(gm, om, amb) <= MAP_TOL
+
+
+def test_tile_mask_and_untouched_tiles():
+    scene = S.tiny_scene(1, n=60)  # sparse: most tiles empty
+    cam = S.tiny_camera(100, 70)
+    gm, mask, st = gpu_maps(scene, cam, with_mask=True)
+    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    H, W = cam.height, cam.width
+    pix_mask = np.kron(mask, np.ones((16, 16), np.uint8))[:H, :W].astype(bool)
+    # every pixel the oracle sees non-zero lies in an active tile
+    assert not np.any((np.abs(om).sum((0, 1)) > 0) & ~pix_mask)
+    # active tiles are written and match; inactive ones are left untouched (NaN fill)
+    assert np.all(np.isnan(gm[:, :, ~pix_mask]))
+    assert np.isfinite(gm[:, :, pix_mask]).all()
+    gm0 = np.where(np.isnan(gm), 0.0, gm)
+    assert map_rel_err(gm0, om, amb) <= MAP_TOL
+    assert st["n_active_tiles"] == int(mask.sum()) < mask.size
+
+
+def test_gradient_maps_1080p_sampled_pixels():
+    scene, cam, _, _ = S.workload("prims1080p")
+    gm, _, st = gpu_maps(scene, cam)
+    assert st["status"] == 0
+    rng = np.random.default_rng(0)
+    H, W = cam.height, cam.width
+    pix = np.concatenate([rng.integers(0, H * W, 3000), [0, W - 1, (H - 1) * W, H * W - 1]])
+    out, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()), pixels=pix)
+    i, j = pix // W, pix % W
+    got = gm[:, :, i, j].transpose(2, 0, 1)
+    ok = amb == 0
+    ref = np.abs(out).max()
+    assert np.abs(got[ok] - out[ok]).max() <= MAP_TOL * ref
+    assert amb.mean() <= 5 * AMB_FRAC_MAX
+
+
+def test_raster_deterministic():
+    scene, cam = _small_prims(n=5000)
+    a, _, _ = gpu_maps(scene, cam)
+    b, _, _ = gpu_maps(scene, cam)
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ Poisson
+
+@pytest.mark.parametrize("hw", [(64, 64), (135, 240), (17, 9), (3, 200), (1, 1), (2, 2), (100, 37),
+                                (33, 16), (270, 481)])
+def test_poisson_matches_dct_oracle(hw):
+    H, W = hw
+    rng = np.random.default_rng(H * 1000 + W)
+    maps = rng.laplace(0, 0.1, (3, 2, H, W)).astype(np.float32)
+    mean = [0.5, 0.1, -0.2]
+    img, st = gpu_poisson(maps, mean)
+    ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), mean)
+    assert st["status"] == 0, st
+    assert img_err(img, ref)[0] <= IMG_TOL
+    assert st["rel_residual"] <= 1e-6
+    np.testing.assert_allclose(img.mean(axis=(1, 2)), mean, atol=1e-6)
+
+
+def test_poisson_recovers_known_image_1080p():
+    H, W = 1080, 1920
+    img0 = np.stack([S.image_from_gradients_test_image(H, W, seed=s) for s in range(3)])
+    maps = O.forward_gradients(img0).astype(np.float32)
+    img, st = gpu_poisson(maps, img0.mean(axis=(1, 2)))
+    ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), img0.mean(axis=(1, 2)))
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6
+    assert st["cycles"] <= 12
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+def test_poisson_zero_field_gives_mean():
+    img, st = gpu_poisson(np.zeros((2, 2, 40, 50), np.float32), [0.25, 0.75])
+    assert st["status"] == 0 and st["cycles"] == 0
+    np.testing.assert_array_equal(img[0], 0.25)
+    np.testing.assert_array_equal(img[1], 0.75)
+
+
+def test_poisson_no_converge_status():
+    rng = np.random.default_rng(1)
+    maps = rng.laplace(0, 0.1, (1, 2, 200, 300)).astype(np.float32)
+    img, st = gpu_poisson(maps, [0.5], G.solver_opts(max_cycles=1, rtol=1e-9))
+    assert st["status"] == G._abi.ERR_NO_CONVERGE
+    assert st["cycles"] == 1 and st["rel_residual"] > 1e-9
+
+
+def test_poisson_nonfinite_status():
+    maps = np.zeros((1, 2, 32, 32), np.float32)
+    maps[0, 0, 5, 5] = np.nan
+    _, st = gpu_poisson(maps, [0.5])
+    assert st["status"] == G._abi.ERR_NONFINITE
+
+
+def test_poisson_mask_reads_inactive_tiles_as_zero():
+    rng = np.random.default_rng(2)
+    H, W = 70, 90
+    maps = rng.laplace(0, 0.1, (3, 2, H, W)).astype(np.float32)
+    mask = (rng.random(((H + 15) // 16, (W + 15) // 16)) < 0.5).astype(np.uint8)
+    pix = np.kron(mask, np.ones((16, 16), np.uint8))[:H, :W].astype(bool)
+    garbage = maps.copy()
+    garbage[:, :, ~pix] = 1e30
+    clean = np.where(pix, maps, 0).astype(np.float32)
+    a, st = gpu_poisson(garbage, [0.5] * 3, mask=mask)
+    b, _ = gpu_poisson(clean, [0.5] * 3)
+    assert st["status"] == 0
+    np.testing.assert_allclose(a, b, atol=1e-6)
+
+
+def test_poisson_coarse_cache_reused_across_sizes():
+    """One workspace solving two different grid shapes in turn (the cached coarse
+    factor is keyed by the shape) gives the same answers as fresh workspaces."""
+    rng = np.random.default_rng(3)
+    m1 = rng.laplace(0, 0.1, (1, 2, 90, 130)).astype(np.float32)
+    m2 = rng.laplace(0, 0.1, (1, 2, 64, 64)).astype(np.float32)
+    nbytes = G.workspace_size(0, 1, 130, 90, None, None)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = []
+    for m in (m1, m2, m1):
+        t = torch.as_tensor(m).cuda()
+        img = torch.empty((1,) + m.shape[2:], device="cuda")
+        G.poisson_reconstruct(t, [0.5], img, ws)
+        assert G.sync_status(ws)["status"] == 0
+        out.append(img.cpu().numpy())
+    assert np.array_equal(out[0], out[2])
+    ref = O.poisson_neumann(O.divergence(m2.astype(np.float64)), [0.5])
+    assert img_err(out[1], ref)[0] <= IMG_TOL
+
+
+# ------------------------------------------------------------------ whole view
+
+def _render(scene, cam, mean, ropts=None, sopts=None, nbytes=None):
+    g = G.gaussians_to_device(scene)
+    ropts = ropts or G.raster_opts()
+    sopts = sopts or G.solver_opts()
+    nb = nbytes or G.workspace_size(scene.n, scene.channels, cam.width, cam.height, ropts, sopts)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    img = torch.empty((scene.channels, cam.height, cam.width), device="cuda")
+    G.render_view(g, cam, mean, img, ws, ropts, sopts)
+    return img.cpu().numpy().astype(np.float64), G.sync_status(ws)
+
+
+def test_render_view_tiny_matches_oracle():
+    scene, cam, mean, rtol = S.workload("tiny64")
+    img, st = _render(scene, cam, mean, sopts=G.solver_opts(rtol=rtol))
+    ref, _, _ = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
+    assert st["status"] == 0, st
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+def test_render_view_1080p_matches_oracle():
+    scene, cam, mean, rtol = S.workload("prims1080p")
+    img, st = _render(scene, cam, mean, sopts=G.solver_opts(rtol=rtol))
+    ref, _, amb = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
+    assert st["status"] == 0 and st["rel_residual"] <= rtol, st
+    rel, absolute = img_err(img, ref)
+    assert rel <= IMG_TOL, (rel, absolute)
+    assert st["n_visible"] > 0.9 * scene.n
+
+
+def test_render_view_empty_and_culled_scenes_give_mean():
+    cam = S.tiny_camera(48, 40)
+    empty = S.tiny_scene(0, n=0)
+    img, st = _render(empty, cam, [0.5, 0.2, 0.1])
+    assert st["status"] == 0
+    np.testing.assert_array_equal(img[1], np.float32(0.2))
+    behind = S.tiny_scene(0, n=50)
+    behind.mean[:, 2] = -10.0  # behind the camera at z = -3
+    img, st = _render(behind, cam, [0.5, 0.2, 0.1])
+    assert st["status"] == 0 and st["n_visible"] == 0
+    np.testing.assert_array_equal(img[0], np.float32(0.5))
+
+
+def test_render_view_capacity_overflow_is_reported():
+    scene, cam, mean, _ = S.workload("tiny64")
+    scene.scale *= 4  # large splats: many tiles each
+    img, st = _render(scene, cam, mean, ropts=G.raster_opts(pairs_per_gaussian=1))
+    assert st["status"] == G._abi.ERR_CAPACITY
+    assert st["n_pairs"] > scene.n
+
+
+def test_render_view_nonfinite_gaussian_is_reported():
+    scene, cam, mean, _ = S.workload("tiny64")
+    scene.mean[7, 1] = np.inf
+    _, st = _render(scene, cam, mean)
+    assert st["status"] == G._abi.ERR_NONFINITE
+
+
+def test_render_view_workspace_too_small_raises():
+    scene, cam, mean, _ = S.workload("tiny64")
+    with pytest.raises(G.GDGSError) as e:
+        _render(scene, cam, mean, nbytes=4096)
+    assert e.value.code == G._abi.ERR_WORKSPACE
