@@ -241,7 +241,7 @@ def image_from_gradients_test_image(h: int, w: int, seed: int = 0) -> np.ndarray
 def workload(name: str):
     """Returns (scene, camera, per-channel mean, solver rtol) of a named workload."""
     if name == "tiny64":
-        return tiny_scene(0), tiny_camera(), np.full(3, 0.5), 1e-8
+        return tiny_scene(0), tiny_camera(), np.full(3, 0.5), 1e-6
     if name == "prims1080p":
         return primitives_scene(0), metric_camera(), np.full(3, 0.5), 1e-6
     if name == "prims4k":

@@ -207,7 +207,7 @@ def test_poisson_coarse_cache_reused_across_sizes():
     rng = np.random.default_rng(3)
     m1 = rng.laplace(0, 0.1, (1, 2, 90, 130)).astype(np.float32)
     m2 = rng.laplace(0, 0.1, (1, 2, 64, 64)).astype(np.float32)
-    nbytes = G.workspace_size(0, 1, 130, 90, None, None)
+    nbytes = max(G.workspace_size(0, 1, 130, 90, None, None), G.workspace_size(0, 1, 64, 64, None, None))
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     out = []
     for m in (m1, m2, m1):
