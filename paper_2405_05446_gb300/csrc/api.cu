@@ -465,8 +465,8 @@ int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream) {
   double rel = 0.0;
   if (c.max_cycles > 0) {  // a solve ran
     const double r0 = c.rnorm2[0];
-    const double rk = c.stopped ? c.rnorm2[c.cycles] : c.final_rnorm2;
-    rel = r0 > 0 ? sqrt(rk / r0) : 0.0;
+    const int kf = c.cycles < 0 ? 0 : (c.cycles > kMaxCycles ? kMaxCycles : c.cycles);
+    rel = r0 > 0 ? sqrt(c.rnorm2[kf] / r0) : 0.0;
     if (status == GDGS_OK && !c.stopped && rel > c.rtol) status = GDGS_ERR_NO_CONVERGE;
   }
   if (stats) {

@@ -24,6 +24,7 @@ std::mutex g_mu;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 thread_local long t_open = -1;
+thread_local bool t_capturing = false;
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -38,9 +39,14 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
+bool diag_profiling() { return g_profiling.load(std::memory_order_acquire) != 0; }
+
+void diag_set_capturing(bool on) { t_capturing = on; }
+
 void diag_before(const char *name, cudaStream_t st) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
   t_open = -1;
+  if (t_capturing) return;  // counted when the graph runs
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_profiling.load(std::memory_order_acquire)) return;
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r{name, take_event(), take_event()};
@@ -63,7 +69,7 @@ using namespace gdgs;
 
 extern "C" {
 
-uint64_t gdgs_kernel_launch_count(void) { return g_launches.load(); }
+uint64_t gdgs_kernel_launch_count(void) { return g_launches.load() + graph_kernel_count(); }
 
 int gdgs_profile_begin(void) {
   std::lock_guard<std::mutex> lk(g_mu);

@@ -31,6 +31,8 @@ struct Ctrl {
   unsigned pad0;
   int max_cycles;
   int channels;
+  int iter;            // cycle index when the cycle loop runs as a graph
+  int pad1;
   double rtol;
   double rnorm2[kMaxCycles + 1];             // ||rho - L u_k||^2, k = 0..
   double sum_u[kMaxCycles + 1][GDGS_MAX_CHANNELS];  // sum of u_k per channel
@@ -41,6 +43,9 @@ struct Ctrl {
 // Diagnostics hooks around every kernel launch (diag.cu).
 void diag_before(const char *name, cudaStream_t st);
 void diag_after(cudaStream_t st);
+bool diag_profiling();
+void diag_set_capturing(bool on);  // launches on this thread are being captured into a graph
+unsigned long long graph_kernel_count();  // kernels run by graph-launched cycle loops
 struct LaunchScope {
   cudaStream_t st;
   LaunchScope(const char *name, cudaStream_t s) : st(s) { diag_before(name, s); }

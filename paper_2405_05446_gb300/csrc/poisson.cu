@@ -37,6 +37,13 @@
 // accumulates ||rho - L u_k||^2; every later kernel of that cycle returns at
 // once when it is <= rtol^2 ||rho||^2, and the first one records the stop, so the
 // remaining launches of the cycle loop do no work.
+#include <stdlib.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -133,66 +140,128 @@ __device__ __forceinline__ bool should_stop(Ctrl *ctrl, int k, int first) {
   return false;
 }
 
+// Block-wide sum; the result is valid in the first thread of the block.
 __device__ float block_sum(float v) {
   __shared__ float part[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  const int lane = tid & 31, w = tid >> 5;
   __syncthreads();
   if (lane == 0) part[w] = v;
   __syncthreads();
   float s = 0.f;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += part[i];
-  return s;  // valid in thread 0
+  if (tid == 0)
+    for (int i = 0; i < (nthreads + 31) / 32; ++i) s += part[i];
+  return s;
 }
 
 // ------------------------------------------------------------------ region helpers
+//
+// Shared-memory region kernels run 256 threads as a 32 x 8 grid (tx, ty). A
+// region has RY x RX cells with origin (ry0, rx0) in level coordinates; rows are
+// walked with stride 8 and columns with stride 32, so every trip count is a
+// compile-time constant. INT marks a block whose whole region lies two cells or
+// more inside the grid: there every face coefficient is 1 and no bounds test is
+// needed.
 
-// One red-black half-sweep over the cells of colour `col` of a shared-memory
-// region (origin (ry0, rx0) in level coordinates, RY x RX cells), restricted to
-// cells at least `s` cells inside the region and inside the grid.
+constexpr int kBX = 32, kBY = 8;
+
 template <int RY, int RX>
+__device__ __forceinline__ bool region_interior(const LevelGeom &g, int ry0, int rx0) {
+  return ry0 >= 1 && rx0 >= 1 && ry0 + RY - 1 <= g.H - 3 && rx0 + RX - 1 <= g.W - 3;
+}
+
+// One red-black half-sweep over the cells of colour `col` at least `s` cells
+// inside the region (and inside the grid).
+template <int RY, int RX, bool INT>
 __device__ __forceinline__ void half_sweep(float *U, const float *F, const LevelGeom &g, int ry0,
                                            int rx0, int s, int col) {
-  const int y1 = RY - s, x1 = RX - s;
-  const int hw = (x1 - s + 1) >> 1;
-  const int cnt = (y1 - s) * hw;
-  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-    const int row = idx / hw;
-    const int m = idx - row * hw;
-    const int yy = s + row;
+  for (int yy = s + threadIdx.y; yy < RY - s; yy += kBY) {
     const int gy = ry0 + yy;
-    const int xx = s + (((gy + rx0 + s) ^ col) & 1) + 2 * m;
-    if (xx >= x1) continue;
-    const int gx = rx0 + xx;
-    if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
-    const int o = yy * RX + xx;
-    U[o] = gs_value(g, gy, gx, U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+    const int x0 = s + (((gy + rx0 + s) ^ col) & 1);
+#pragma unroll
+    for (int j = 0; j < (RX + 2 * kBX - 1) / (2 * kBX); ++j) {
+      const int xx = x0 + 2 * (threadIdx.x + kBX * j);
+      if (xx < RX - s) {
+        const int o = yy * RX + xx;
+        if (INT) {
+          U[o] = 0.25f * ((U[o + 1] + U[o - 1]) + (U[o + RX] + U[o - RX]) - F[o]);
+        } else {
+          const int gx = rx0 + xx;
+          if (gy >= 0 && gy < g.H && gx >= 0 && gx < g.W)
+            U[o] = gs_value(g, gy, gx, U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+        }
+      }
+    }
   }
 }
 
 template <int RY, int RX>
-__device__ __forceinline__ void load_region(float *dst, const float *src, const LevelGeom &g,
-                                            int ry0, int rx0) {
-  for (int idx = threadIdx.x; idx < RY * RX; idx += blockDim.x) {
-    const int yy = idx / RX, xx = idx - yy * RX;
-    const int gy = ry0 + yy, gx = rx0 + xx;
-    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-    dst[idx] = in ? src[(size_t)gy * g.W + gx] : 0.f;
+__device__ __forceinline__ void load_region(float *dst, const float *__restrict__ src,
+                                            const LevelGeom &g, int ry0, int rx0) {
+  for (int yy = threadIdx.y; yy < RY; yy += kBY) {
+    const int gy = ry0 + yy;
+    const bool rin = gy >= 0 && gy < g.H;
+    for (int xx = threadIdx.x; xx < RX; xx += kBX) {
+      const int gx = rx0 + xx;
+      dst[yy * RX + xx] = (rin && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) : 0.f;
+    }
   }
 }
 
-// Residual of (U, F) on the children of each coarse cell of the output tile,
-// summed into the coarse right-hand side.
-template <int RY, int RX, int HALO>
+template <int RY, int RX>
+__device__ __forceinline__ void zero_region(float *dst) {
+  for (int yy = threadIdx.y; yy < RY; yy += kBY)
+    for (int xx = threadIdx.x; xx < RX; xx += kBX) dst[yy * RX + xx] = 0.f;
+}
+
+// R = rho - L u on the cells one or more inside the region, u = hi + lo read
+// through the read-only cache; R must already hold rho. Float-float sums keep
+// the residual of an iterate whose FP32 rounding alone would exceed the target.
+template <int RY, int RX, bool INT>
+__device__ __forceinline__ void residual_ds(float *R, const float *__restrict__ uhi,
+                                            const float *__restrict__ ulo, const LevelGeom &g,
+                                            int ry0, int rx0) {
+  for (int yy = 1 + threadIdx.y; yy < RY - 1; yy += kBY) {
+    const int gy = ry0 + yy;
+    for (int xx = 1 + threadIdx.x; xx < RX - 1; xx += kBX) {
+      const int gx = rx0 + xx;
+      if (!INT && (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W)) continue;
+      const size_t p = (size_t)gy * g.W + gx;
+      const float hi = __ldg(uhi + p), lo = __ldg(ulo + p);
+      float sh, sl;
+      if (INT) {
+        sh = ((__ldg(uhi + p + 1) - hi) + (__ldg(uhi + p - 1) - hi)) +
+             ((__ldg(uhi + p + g.W) - hi) + (__ldg(uhi + p - g.W) - hi));
+        sl = ((__ldg(ulo + p + 1) - lo) + (__ldg(ulo + p - 1) - lo)) +
+             ((__ldg(ulo + p + g.W) - lo) + (__ldg(ulo + p - g.W) - lo));
+      } else {
+        sh = 0.f;
+        sl = 0.f;
+        if (gx + 1 < g.W) { sh += __ldg(uhi + p + 1) - hi; sl += __ldg(ulo + p + 1) - lo; }
+        if (gx > 0) { sh += __ldg(uhi + p - 1) - hi; sl += __ldg(ulo + p - 1) - lo; }
+        if (gy + 1 < g.H) { sh += __ldg(uhi + p + g.W) - hi; sl += __ldg(ulo + p + g.W) - lo; }
+        if (gy > 0) { sh += __ldg(uhi + p - g.W) - hi; sl += __ldg(ulo + p - g.W) - lo; }
+      }
+      const int o = yy * RX + xx;
+      R[o] = R[o] - (sh + sl);
+    }
+  }
+}
+
+// Residual of (U, F) on the four children of each coarse cell under the output
+// tile, summed into the coarse right-hand side. Thread (tx, ty) owns coarse
+// column tx and rows ty, ty + 8.
+template <int RY, int RX, int HALO, bool INT>
 __device__ __forceinline__ void restrict_tile(const float *U, const float *F, const LevelGeom &g,
                                               const LevelGeom &gc, int ty0, int tx0, float *fc) {
-  constexpr int CY = TY / 2, CX = TX / 2;
   const int ry0 = ty0 - HALO, rx0 = tx0 - HALO;
-  for (int idx = threadIdx.x; idx < CY * CX; idx += blockDim.x) {
-    const int ci = idx / CX, cj = idx - ci * CX;
-    const int CI = (ty0 >> 1) + ci, CJ = (tx0 >> 1) + cj;
+  const int CJ = (tx0 >> 1) + threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < TY / 2 / kBY; ++i) {
+    const int CI = (ty0 >> 1) + threadIdx.y + kBY * i;
     if (CI >= gc.H || CJ >= gc.W) continue;
     float sum = 0.f;
 #pragma unroll
@@ -200,9 +269,12 @@ __device__ __forceinline__ void restrict_tile(const float *U, const float *F, co
 #pragma unroll
       for (int dj = 0; dj < 2; ++dj) {
         const int gy = 2 * CI + di, gx = 2 * CJ + dj;
-        if (gy >= g.H || gx >= g.W) continue;
         const int o = (gy - ry0) * RX + (gx - rx0);
-        sum += residual(g, gy, gx, U[o], U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+        if (INT) {
+          sum += F[o] - ((U[o + 1] + U[o - 1]) + (U[o + RX] + U[o - RX]) - 4.f * U[o]);
+        } else if (gy < g.H && gx < g.W) {
+          sum += residual(g, gy, gx, U[o], U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
+        }
       }
     fc[(size_t)CI * gc.W + CJ] = sum;
   }
@@ -222,33 +294,51 @@ __device__ __forceinline__ CoarseBox coarse_box(int ry0, int rx0, int RY, int RX
   return b;
 }
 
-__device__ __forceinline__ void load_coarse(float *EC, const float *uc, const LevelGeom &gc,
-                                            const CoarseBox &b) {
-  for (int idx = threadIdx.x; idx < b.CRY * b.CRX; idx += blockDim.x) {
-    const int yy = idx / b.CRX, xx = idx - yy * b.CRX;
-    const int gy = b.cy0 + yy, gx = b.cx0 + xx;
-    const bool in = gy >= 0 && gy < gc.H && gx >= 0 && gx < gc.W;
-    EC[idx] = in ? uc[(size_t)gy * gc.W + gx] : 0.f;
+__device__ __forceinline__ void load_coarse(float *EC, const float *__restrict__ uc,
+                                            const LevelGeom &gc, const CoarseBox &b) {
+  for (int yy = threadIdx.y; yy < b.CRY; yy += kBY) {
+    const int gy = b.cy0 + yy;
+    const bool rin = gy >= 0 && gy < gc.H;
+    for (int xx = threadIdx.x; xx < b.CRX; xx += kBX) {
+      const int gx = b.cx0 + xx;
+      EC[yy * b.CRX + xx] = (rin && gx >= 0 && gx < gc.W) ? __ldg(uc + (size_t)gy * gc.W + gx) : 0.f;
+    }
   }
 }
 
-// U += P(EC) on every in-grid cell of the region.
+// U += P(EC) on every in-grid cell of the region; column weights are computed
+// once per thread, row weights once per row.
 template <int RY, int RX>
 __device__ __forceinline__ void prolong_region(float *U, const float *EC, const LevelGeom &g,
                                                const LevelGeom &gc, const CoarseBox &b, int ry0,
                                                int rx0) {
-  for (int idx = threadIdx.x; idx < RY * RX; idx += blockDim.x) {
-    const int yy = idx / RX, xx = idx - yy * RX;
-    const int gy = ry0 + yy, gx = rx0 + xx;
-    if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
+  constexpr int NJ = (RX + kBX - 1) / kBX;
+  int j0[NJ], j1[NJ];
+  float wx[NJ];
+  bool cin[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int xx = threadIdx.x + kBX * j;
+    const int gx = rx0 + xx;
+    cin[j] = xx < RX && gx >= 0 && gx < g.W;
+    const P1 px = prolong1d(cin[j] ? gx : 0, g.shift, g.W0, gc.W);
+    j0[j] = px.i0 - b.cx0;
+    j1[j] = px.i1 - b.cx0;
+    wx[j] = px.w1;
+  }
+  for (int yy = threadIdx.y; yy < RY; yy += kBY) {
+    const int gy = ry0 + yy;
+    if (gy < 0 || gy >= g.H) continue;
     const P1 py = prolong1d(gy, g.shift, g.H0, gc.H);
-    const P1 px = prolong1d(gx, g.shift, g.W0, gc.W);
     const float *r0 = EC + (py.i0 - b.cy0) * b.CRX;
     const float *r1 = EC + (py.i1 - b.cy0) * b.CRX;
-    const int j0 = px.i0 - b.cx0, j1 = px.i1 - b.cx0;
-    const float a0 = r0[j0] + px.w1 * (r0[j1] - r0[j0]);
-    const float a1 = r1[j0] + px.w1 * (r1[j1] - r1[j0]);
-    U[idx] += a0 + py.w1 * (a1 - a0);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (!cin[j]) continue;
+      const float a0 = r0[j0[j]] + wx[j] * (r0[j1[j]] - r0[j0[j]]);
+      const float a1 = r1[j0[j]] + wx[j] * (r1[j1[j]] - r1[j0[j]]);
+      U[yy * RX + threadIdx.x + kBX * j] += a0 + py.w1 * (a1 - a0);
+    }
   }
 }
 
@@ -266,151 +356,147 @@ template <int NU>
 struct L0DownShape {
   static constexpr int H = 2 * NU + 1;
   static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
-  static constexpr size_t smem = 4 * RN * sizeof(float);
+  static constexpr size_t smem = 2 * RN * sizeof(float);
 };
+
+__device__ __forceinline__ int cycle_index(const Ctrl *ctrl, int k) { return k >= 0 ? k : ctrl->iter; }
 
 // Finest level, first half of a cycle: r_k = rho - L u_k in float-float, its
 // norm, nu1 sweeps on L e = r_k from e = 0, then restriction of r_k - L e.
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg0_down_kernel(L0Args a, Ctrl *ctrl, int k) {
+template <int NU, bool INT>
+__device__ __forceinline__ void mg0_down_body(const L0Args &a, Ctrl *ctrl, int k, float *R, float *E) {
   using S = L0DownShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
-  extern __shared__ float sm[];
-  float *R = sm, *E = sm + RN, *UH = sm + 2 * RN, *UL = sm + 3 * RN;
-  if (k > 0 && *(volatile int *)&ctrl->stopped) return;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX;
   const LevelGeom &g = a.g0;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ry0 = ty0 - H, rx0 = tx0 - H;
   const size_t cb = (size_t)c * g.plane;
-  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
-    const int yy = idx / RX, xx = idx - yy * RX;
-    const int gy = ry0 + yy, gx = rx0 + xx;
-    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-    const size_t o = cb + (size_t)gy * g.W + gx;
-    R[idx] = in ? a.rho[o] : 0.f;
-    E[idx] = 0.f;
-    if (k > 0) {
-      UH[idx] = in ? a.uhi[o] : 0.f;
-      UL[idx] = in ? a.ulo[o] : 0.f;
-    }
-  }
+  load_region<RY, RX>(R, a.rho + cb, g, ry0, rx0);
+  zero_region<RY, RX>(E);
   __syncthreads();
   if (k > 0) {
-    for (int idx = threadIdx.x; idx < (RY - 2) * (RX - 2); idx += blockDim.x) {
-      const int yy = 1 + idx / (RX - 2), xx = 1 + idx % (RX - 2);
-      const int gy = ry0 + yy, gx = rx0 + xx;
-      if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
-      const int o = yy * RX + xx;
-      const float hi = UH[o], lo = UL[o];
-      float sh = 0.f, sl = 0.f;
-      if (gx + 1 < g.W) { sh += UH[o + 1] - hi; sl += UL[o + 1] - lo; }
-      if (gx > 0) { sh += UH[o - 1] - hi; sl += UL[o - 1] - lo; }
-      if (gy + 1 < g.H) { sh += UH[o + RX] - hi; sl += UL[o + RX] - lo; }
-      if (gy > 0) { sh += UH[o - RX] - hi; sl += UL[o - RX] - lo; }
-      R[o] = R[o] - (sh + sl);
-    }
+    residual_ds<RY, RX, INT>(R, a.uhi + cb, a.ulo + cb, g, ry0, rx0);
     __syncthreads();
   }
-  // ||r_k||^2 over the output tile
-  float nrm = 0.f;
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    const int ty = idx / TX, tx = idx - ty * TX;
-    const int gy = ty0 + ty, gx = tx0 + tx;
-    if (gy < g.H && gx < g.W) {
-      const float r = R[(ty + H) * RX + tx + H];
-      nrm = fmaf(r, r, nrm);
-    }
+  if (k == 0) {  // ||rho||^2; later norms come from the previous cycle's up kernel
+    float nrm = 0.f;
+#pragma unroll
+    for (int i = 0; i < TY / kBY; ++i)
+#pragma unroll
+      for (int j = 0; j < TX / kBX; ++j) {
+        const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
+        if (INT || (ty0 + ty < g.H && tx0 + tx < g.W)) {
+          const float r = R[(ty + H) * RX + tx + H];
+          nrm = fmaf(r, r, nrm);
+        }
+      }
+    nrm = block_sum(nrm);
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[0], (double)nrm);
   }
-  nrm = block_sum(nrm);
-  if (threadIdx.x == 0) atomicAdd(&ctrl->rnorm2[k], (double)nrm);
-  // pre-smoothing of the correction
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX>(E, R, g, ry0, rx0, s + 1, s & 1);
+    half_sweep<RY, RX, INT>(E, R, g, ry0, rx0, s + 1, s & 1);
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    const int ty = idx / TX, tx = idx - ty * TX;
-    const int gy = ty0 + ty, gx = tx0 + tx;
-    if (gy < g.H && gx < g.W) a.e0[cb + (size_t)gy * g.W + gx] = E[(ty + H) * RX + tx + H];
-  }
-  restrict_tile<RY, RX, H>(E, R, g, a.g1, ty0, tx0, a.f1 + (size_t)c * a.g1.plane);
+  float *e0 = a.e0 + cb;
+#pragma unroll
+  for (int i = 0; i < TY / kBY; ++i)
+#pragma unroll
+    for (int j = 0; j < TX / kBX; ++j) {
+      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
+      const int gy = ty0 + ty, gx = tx0 + tx;
+      if (INT || (gy < g.H && gx < g.W)) e0[(size_t)gy * g.W + gx] = E[(ty + H) * RX + tx + H];
+    }
+  restrict_tile<RY, RX, H, INT>(E, R, g, a.g1, ty0, tx0, a.f1 + (size_t)c * a.g1.plane);
+}
+
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg0_down_kernel(L0Args a, Ctrl *ctrl, int k_in) {
+  using S = L0DownShape<NU>;
+  extern __shared__ float sm[];
+  if (*(volatile int *)&ctrl->stopped) return;
+  const int k = cycle_index(ctrl, k_in);
+  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
+  if (region_interior<S::RY, S::RX>(a.g0, ry0, rx0))
+    mg0_down_body<NU, true>(a, ctrl, k, sm, sm + S::RN);
+  else
+    mg0_down_body<NU, false>(a, ctrl, k, sm, sm + S::RN);
 }
 
 template <int NU>
 struct L0UpShape {
-  static constexpr int H = 2 * NU;
+  static constexpr int H = 2 * NU + 1;
   static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
   static constexpr int CRN = (RY / 2 + 4) * (RX / 2 + 4);
-  static constexpr size_t smem = (4 * RN + CRN) * sizeof(float);
+  static constexpr size_t smem = (2 * RN + CRN) * sizeof(float);
 };
 
 // Finest level, second half: e += P e_1, nu2 sweeps on L e = r_k (r_k recomputed
-// from u_k and rho), u_{k+1} = u_k + e in float-float, and sum(u_{k+1}).
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg0_up_kernel(L0Args a, Ctrl *ctrl, int k) {
+// from u_k and rho), u_{k+1} = u_k + e in float-float, sum(u_{k+1}) and
+// ||r_{k+1}||^2 with r_{k+1} = r_k - L e (u_{k+1} is the exact float-float sum,
+// so this is its residual up to FP32 rounding of r_k - L e).
+template <int NU, bool INT>
+__device__ __forceinline__ void mg0_up_body(const L0Args &a, Ctrl *ctrl, int k, float *R, float *E,
+                                            float *EC) {
   using S = L0UpShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
-  extern __shared__ float sm[];
-  float *R = sm, *E = sm + RN, *UH = sm + 2 * RN, *UL = sm + 3 * RN, *EC = sm + 4 * RN;
-  if (should_stop(ctrl, k, 0)) return;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX;
   const LevelGeom &g = a.g0;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ry0 = ty0 - H, rx0 = tx0 - H;
   const size_t cb = (size_t)c * g.plane;
-  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
-    const int yy = idx / RX, xx = idx - yy * RX;
-    const int gy = ry0 + yy, gx = rx0 + xx;
-    const bool in = gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-    const size_t o = cb + (size_t)gy * g.W + gx;
-    R[idx] = in ? a.rho[o] : 0.f;
-    E[idx] = in ? a.e0[o] : 0.f;
-    UH[idx] = (in && k > 0) ? a.uhi[o] : 0.f;
-    UL[idx] = (in && k > 0) ? a.ulo[o] : 0.f;
-  }
+  load_region<RY, RX>(R, a.rho + cb, g, ry0, rx0);
+  load_region<RY, RX>(E, a.e0 + cb, g, ry0, rx0);
   const CoarseBox b = coarse_box(ry0, rx0, RY, RX);
   load_coarse(EC, a.u1 + (size_t)c * a.g1.plane, a.g1, b);
   __syncthreads();
-  if (k > 0) {
-    for (int idx = threadIdx.x; idx < (RY - 2) * (RX - 2); idx += blockDim.x) {
-      const int yy = 1 + idx / (RX - 2), xx = 1 + idx % (RX - 2);
-      const int gy = ry0 + yy, gx = rx0 + xx;
-      if (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) continue;
-      const int o = yy * RX + xx;
-      const float hi = UH[o], lo = UL[o];
-      float sh = 0.f, sl = 0.f;
-      if (gx + 1 < g.W) { sh += UH[o + 1] - hi; sl += UL[o + 1] - lo; }
-      if (gx > 0) { sh += UH[o - 1] - hi; sl += UL[o - 1] - lo; }
-      if (gy + 1 < g.H) { sh += UH[o + RX] - hi; sl += UL[o + RX] - lo; }
-      if (gy > 0) { sh += UH[o - RX] - hi; sl += UL[o - RX] - lo; }
-      R[o] = R[o] - (sh + sl);
-    }
-  }
+  if (k > 0) residual_ds<RY, RX, INT>(R, a.uhi + cb, a.ulo + cb, g, ry0, rx0);
   prolong_region<RY, RX>(E, EC, g, a.g1, b, ry0, rx0);
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX>(E, R, g, ry0, rx0, s + 1, s & 1);
+    half_sweep<RY, RX, INT>(E, R, g, ry0, rx0, s + 1, s & 1);
     __syncthreads();
   }
-  float su = 0.f;
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    const int ty = idx / TX, tx = idx - ty * TX;
-    const int gy = ty0 + ty, gx = tx0 + tx;
-    if (gy < g.H && gx < g.W) {
-      const int o = (ty + H) * RX + tx + H;
-      float hi = UH[o], lo = UL[o];
-      ds_add(hi, lo, E[o]);
-      const size_t go = cb + (size_t)gy * g.W + gx;
-      a.uhi[go] = hi;
-      a.ulo[go] = lo;
-      su += hi + lo;
+  float su = 0.f, rn2 = 0.f;
+  float *uh = a.uhi + cb, *ul = a.ulo + cb;
+#pragma unroll
+  for (int i = 0; i < TY / kBY; ++i)
+#pragma unroll
+    for (int j = 0; j < TX / kBX; ++j) {
+      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
+      const int gy = ty0 + ty, gx = tx0 + tx;
+      if (INT || (gy < g.H && gx < g.W)) {
+        const size_t p = (size_t)gy * g.W + gx;
+        const int o = (ty + H) * RX + tx + H;
+        float hi = k > 0 ? uh[p] : 0.f, lo = k > 0 ? ul[p] : 0.f;
+        ds_add(hi, lo, E[o]);
+        uh[p] = hi;
+        ul[p] = lo;
+        su += hi + lo;
+        const float rn = INT ? R[o] - ((E[o + 1] + E[o - 1]) + (E[o + RX] + E[o - RX]) - 4.f * E[o])
+                             : residual(g, gy, gx, E[o], E[o + 1], E[o - 1], E[o + RX], E[o - RX], R[o]);
+        rn2 = fmaf(rn, rn, rn2);
+      }
     }
-  }
   su = block_sum(su);
-  if (threadIdx.x == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+  rn2 = block_sum(rn2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+}
+
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg0_up_kernel(L0Args a, Ctrl *ctrl, int k_in) {
+  using S = L0UpShape<NU>;
+  extern __shared__ float sm[];
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, 0)) return;
+  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
+  if (region_interior<S::RY, S::RX>(a.g0, ry0, rx0))
+    mg0_up_body<NU, true>(a, ctrl, k, sm, sm + S::RN, sm + 2 * S::RN);
+  else
+    mg0_up_body<NU, false>(a, ctrl, k, sm, sm + S::RN, sm + 2 * S::RN);
 }
 
 struct LvArgs {
@@ -427,33 +513,46 @@ struct LvDownShape {
   static constexpr size_t smem = 2 * RN * sizeof(float);
 };
 
-// Level l >= 1, down: nu1 sweeps from u = 0 and residual restriction.
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k, int first) {
+template <int NU, bool INT>
+__device__ __forceinline__ void mg_down_body(const LvArgs &a, float *F, float *U) {
   using S = LvDownShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
-  extern __shared__ float sm[];
-  float *F = sm, *U = sm + RN;
-  if (should_stop(ctrl, k, first)) return;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX;
   const LevelGeom &g = a.g;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ry0 = ty0 - H, rx0 = tx0 - H;
   load_region<RY, RX>(F, a.f + (size_t)c * g.plane, g, ry0, rx0);
-  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) U[idx] = 0.f;
+  zero_region<RY, RX>(U);
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX>(U, F, g, ry0, rx0, s + 1, s & 1);
+    half_sweep<RY, RX, INT>(U, F, g, ry0, rx0, s + 1, s & 1);
     __syncthreads();
   }
   float *uo = a.u + (size_t)c * g.plane;
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    const int ty = idx / TX, tx = idx - ty * TX;
-    const int gy = ty0 + ty, gx = tx0 + tx;
-    if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
-  }
-  restrict_tile<RY, RX, H>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
+#pragma unroll
+  for (int i = 0; i < TY / kBY; ++i)
+#pragma unroll
+    for (int j = 0; j < TX / kBX; ++j) {
+      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
+      const int gy = ty0 + ty, gx = tx0 + tx;
+      if (INT || (gy < g.H && gx < g.W)) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
+    }
+  restrict_tile<RY, RX, H, INT>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
+}
+
+// Level l >= 1, down: nu1 sweeps from u = 0 and residual restriction.
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k_in, int first) {
+  using S = LvDownShape<NU>;
+  extern __shared__ float sm[];
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, first)) return;
+  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
+  if (region_interior<S::RY, S::RX>(a.g, ry0, rx0))
+    mg_down_body<NU, true>(a, sm, sm + S::RN);
+  else
+    mg_down_body<NU, false>(a, sm, sm + S::RN);
 }
 
 template <int NU>
@@ -464,14 +563,10 @@ struct LvUpShape {
   static constexpr size_t smem = (2 * RN + CRN) * sizeof(float);
 };
 
-// Level l >= 1, up: u += P u_{l+1}, nu2 sweeps.
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k) {
+template <int NU, bool INT>
+__device__ __forceinline__ void mg_up_body(const LvArgs &a, float *F, float *U, float *EC) {
   using S = LvUpShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX, RN = S::RN;
-  extern __shared__ float sm[];
-  float *F = sm, *U = sm + RN, *EC = sm + 2 * RN;
-  if (should_stop(ctrl, k, 0)) return;
+  constexpr int H = S::H, RY = S::RY, RX = S::RX;
   const LevelGeom &g = a.g;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
@@ -485,18 +580,37 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX>(U, F, g, ry0, rx0, s + 1, s & 1);
+    half_sweep<RY, RX, INT>(U, F, g, ry0, rx0, s + 1, s & 1);
     __syncthreads();
   }
   float *uo = a.u + (size_t)c * g.plane;
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    const int ty = idx / TX, tx = idx - ty * TX;
-    const int gy = ty0 + ty, gx = tx0 + tx;
-    if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
-  }
+#pragma unroll
+  for (int i = 0; i < TY / kBY; ++i)
+#pragma unroll
+    for (int j = 0; j < TX / kBX; ++j) {
+      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
+      const int gy = ty0 + ty, gx = tx0 + tx;
+      if (INT || (gy < g.H && gx < g.W)) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
+    }
+}
+
+// Level l >= 1, up: u += P u_{l+1}, nu2 sweeps.
+template <int NU>
+__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
+  using S = LvUpShape<NU>;
+  extern __shared__ float sm[];
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, 0)) return;
+  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
+  if (region_interior<S::RY, S::RX>(a.g, ry0, rx0))
+    mg_up_body<NU, true>(a, sm, sm + S::RN, sm + 2 * S::RN);
+  else
+    mg_up_body<NU, false>(a, sm, sm + S::RN, sm + 2 * S::RN);
 }
 
 // ------------------------------------------------------------------ tail (one CTA per channel)
+//
+// 1024 threads as 32 x 32; levels lt..L live in shared memory as dense arrays.
 
 struct TailArgs {
   int lt, L;
@@ -512,28 +626,32 @@ __device__ __forceinline__ float tail_nb(const float *U, const LevelGeom &g, int
   return (I >= 0 && I < g.H && J >= 0 && J < g.W) ? U[I * g.W + J] : 0.f;
 }
 
-__device__ void tail_half_sweep(float *U, const float *F, const LevelGeom &g, int col) {
-  const int hw = (g.W + 1) >> 1;
-  for (int idx = threadIdx.x; idx < g.H * hw; idx += blockDim.x) {
-    const int I = idx / hw, m = idx - I * hw;
-    const int J = ((I ^ col) & 1) + 2 * m;
-    if (J >= g.W) continue;
-    const int o = I * g.W + J;
-    U[o] = gs_value(g, I, J, tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
-                    tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[o]);
+__device__ __forceinline__ void tail_half_sweep(float *U, const float *F, const LevelGeom &g, int col) {
+  for (int I = threadIdx.y; I < g.H; I += 32) {
+    const int p = (I ^ col) & 1;
+    for (int J = p + 2 * threadIdx.x; J < g.W; J += 64) {
+      const int o = I * g.W + J;
+      if (interior(g, I, J))
+        U[o] = 0.25f * ((U[o + 1] + U[o - 1]) + (U[o + g.W] + U[o - g.W]) - F[o]);
+      else
+        U[o] = gs_value(g, I, J, tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
+                        tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[o]);
+    }
   }
 }
 
 template <int NU1, int NU2>
-__global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k, int first) {
+__global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
   extern __shared__ float sm[];
+  const int k = cycle_index(ctrl, k_in);
   if (should_stop(ctrl, k, first)) return;
   const int c = blockIdx.x;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   {
     const LevelGeom &g = a.g[a.lt];
     float *F = sm + a.off[a.lt] + g.H * g.W;
     const float *src = a.f_lt + (size_t)c * g.plane;
-    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) F[i] = src[i];
+    for (int i = tid; i < g.H * g.W; i += kTailThreads) F[i] = __ldg(src + i);
   }
   __syncthreads();
   for (int l = a.lt; l < a.L; ++l) {
@@ -541,34 +659,37 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
     const LevelGeom &gc = a.g[l + 1];
     float *U = sm + a.off[l], *F = U + g.H * g.W;
     float *Fc = sm + a.off[l + 1] + gc.H * gc.W;
-    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) U[i] = 0.f;
+    for (int i = tid; i < g.H * g.W; i += kTailThreads) U[i] = 0.f;
     __syncthreads();
     for (int s = 0; s < 2 * NU1; ++s) {
       tail_half_sweep(U, F, g, s & 1);
       __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < gc.H * gc.W; idx += blockDim.x) {
-      const int CI = idx / gc.W, CJ = idx - CI * gc.W;
-      float sum = 0.f;
-      for (int di = 0; di < 2; ++di)
-        for (int dj = 0; dj < 2; ++dj) {
-          const int I = 2 * CI + di, J = 2 * CJ + dj;
-          if (I >= g.H || J >= g.W) continue;
-          sum += residual(g, I, J, U[I * g.W + J], tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
-                          tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[I * g.W + J]);
-        }
-      Fc[idx] = sum;
-    }
+    for (int CI = threadIdx.y; CI < gc.H; CI += 32)
+      for (int CJ = threadIdx.x; CJ < gc.W; CJ += 32) {
+        float sum = 0.f;
+        for (int di = 0; di < 2; ++di)
+          for (int dj = 0; dj < 2; ++dj) {
+            const int I = 2 * CI + di, J = 2 * CJ + dj;
+            if (I >= g.H || J >= g.W) continue;
+            sum += residual(g, I, J, U[I * g.W + J], tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
+                            tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[I * g.W + J]);
+          }
+        Fc[CI * gc.W + CJ] = sum;
+      }
     __syncthreads();
   }
-  {  // direct FP64 solve on the coarsest grid: u = Minv (-f)
+  {  // direct FP64 solve on the coarsest grid: u = Minv (-f), one warp per row
     const LevelGeom &g = a.g[a.L];
     float *U = sm + a.off[a.L], *F = U + g.H * g.W;
-    for (int i = threadIdx.x; i < a.nc; i += blockDim.x) {
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    for (int i = warp; i < a.nc; i += 32) {
       const double *row = a.Minv + (size_t)i * a.nc;
       double acc = 0.0;
-      for (int j = 0; j < a.nc; ++j) acc = fma(row[j], -(double)F[j], acc);
-      U[i] = (float)acc;
+      for (int j = lane; j < a.nc; j += 32) acc = fma(__ldg(row + j), -(double)F[j], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) U[i] = (float)acc;
     }
     __syncthreads();
   }
@@ -577,14 +698,15 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
     const LevelGeom &gc = a.g[l + 1];
     float *U = sm + a.off[l], *F = U + g.H * g.W;
     const float *Uc = sm + a.off[l + 1];
-    for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
-      const int I = idx / g.W, J = idx - I * g.W;
+    for (int I = threadIdx.y; I < g.H; I += 32) {
       const P1 py = prolong1d(I, g.shift, g.H0, gc.H);
-      const P1 px = prolong1d(J, g.shift, g.W0, gc.W);
       const float *r0 = Uc + py.i0 * gc.W, *r1 = Uc + py.i1 * gc.W;
-      const float a0 = r0[px.i0] + px.w1 * (r0[px.i1] - r0[px.i0]);
-      const float a1 = r1[px.i0] + px.w1 * (r1[px.i1] - r1[px.i0]);
-      U[idx] += a0 + py.w1 * (a1 - a0);
+      for (int J = threadIdx.x; J < g.W; J += 32) {
+        const P1 px = prolong1d(J, g.shift, g.W0, gc.W);
+        const float a0 = r0[px.i0] + px.w1 * (r0[px.i1] - r0[px.i0]);
+        const float a1 = r1[px.i0] + px.w1 * (r1[px.i1] - r1[px.i0]);
+        U[I * g.W + J] += a0 + py.w1 * (a1 - a0);
+      }
     }
     __syncthreads();
     for (int s = 0; s < 2 * NU2; ++s) {
@@ -596,7 +718,7 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
     const LevelGeom &g = a.g[a.lt];
     const float *U = sm + a.off[a.lt];
     float *dst = a.u_lt + (size_t)c * g.plane;
-    for (int i = threadIdx.x; i < g.H * g.W; i += blockDim.x) dst[i] = U[i];
+    for (int i = tid; i < g.H * g.W; i += kTailThreads) dst[i] = U[i];
   }
 }
 
@@ -698,41 +820,25 @@ __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) 
 
 struct FinArgs {
   LevelGeom g0;
-  const float *rho, *uhi, *ulo;
+  const float *uhi, *ulo;
   float *image;
   float mean[GDGS_MAX_CHANNELS];
 };
 
-// image = u + (m_c - mean(u_c)); the residual of u when the loop ran out of cycles.
+// image = u + (m_c - mean(u_c)) for the iterate the cycle loop stopped at.
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   const int stopped = ctrl->stopped;
   const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
   const int c = blockIdx.y;
   const LevelGeom &g = a.g0;
   const size_t plane = (size_t)g.H * g.W;
-  const double npx = (double)plane;
-  const float shift = (float)((double)a.mean[c] - ctrl->sum_u[kf][c] / npx);
+  const float shift = (float)((double)a.mean[c] - ctrl->sum_u[kf][c] / (double)plane);
   const size_t cb = (size_t)c * plane;
-  float r2 = 0.f;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
        p += (size_t)gridDim.x * blockDim.x) {
     const float hi = kf > 0 ? a.uhi[cb + p] : 0.f;
     const float lo = kf > 0 ? a.ulo[cb + p] : 0.f;
     a.image[cb + p] = hi + (lo + shift);
-    if (!stopped && kf > 0) {
-      const int i = (int)(p / g.W), j = (int)(p - (size_t)i * g.W);
-      float sh = 0.f, sl = 0.f;
-      if (j + 1 < g.W) { sh += a.uhi[cb + p + 1] - hi; sl += a.ulo[cb + p + 1] - lo; }
-      if (j > 0) { sh += a.uhi[cb + p - 1] - hi; sl += a.ulo[cb + p - 1] - lo; }
-      if (i + 1 < g.H) { sh += a.uhi[cb + p + g.W] - hi; sl += a.ulo[cb + p + g.W] - lo; }
-      if (i > 0) { sh += a.uhi[cb + p - g.W] - hi; sl += a.ulo[cb + p - g.W] - lo; }
-      const float r = a.rho[cb + p] - (sh + sl);
-      r2 = fmaf(r, r, r2);
-    }
-  }
-  if (!stopped && kf > 0) {
-    r2 = block_sum(r2);
-    if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctrl->mean_set[c] = a.mean[c];
@@ -740,60 +846,99 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   }
 }
 
+// Kernels executed inside graph-launched cycle loops (read by the diagnostics).
+__device__ unsigned long long g_graph_kernels = 0;
+
+// End of cycle k: stop once ||r_{k+1}|| <= rtol ||rho||, advance the cycle
+// index, and (inside a graph) set the loop condition.
+__global__ void advance_kernel(Ctrl *ctrl, int k_in, cudaGraphConditionalHandle h, int in_graph,
+                               unsigned kernels_per_cycle) {
+  const int k = k_in >= 0 ? k_in : ctrl->iter;
+  if (!ctrl->stopped) {
+    const double thr = ctrl->rtol * ctrl->rtol * ctrl->rnorm2[0];
+    if (ctrl->rnorm2[k + 1] <= thr) {
+      ctrl->stopped = 1;
+      ctrl->cycles = k + 1;
+    }
+  }
+  ctrl->iter = k + 1;
+  if (in_graph) {
+    atomicAdd(&g_graph_kernels, (unsigned long long)kernels_per_cycle);
+    cudaGraphSetConditional(h, (!ctrl->stopped && k + 1 < ctrl->max_cycles) ? 1u : 0u);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
+// Opt a kernel in to large dynamic shared memory, once per kernel and device,
+// at the device's per-block maximum (launches then request what they need).
+template <auto Kern>
+cudaError_t set_smem(size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, Kern);
+  if (e != cudaSuccess) return e;
+  const int mx = optin - (int)fa.sharedSizeBytes;
+  if (mx < (int)bytes) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 template <int NU>
 cudaError_t launch_mg0_down(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
   const size_t sm = L0DownShape<NU>::smem;
-  cudaError_t e = set_smem(mg0_down_kernel<NU>, sm);
+  cudaError_t e = set_smem<mg0_down_kernel<NU>>(sm);
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg0_down", st); mg0_down_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  { LaunchScope ls_("mg0_down", st); mg0_down_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
   return cudaGetLastError();
 }
 
 template <int NU>
 cudaError_t launch_mg0_up(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
   const size_t sm = L0UpShape<NU>::smem;
-  cudaError_t e = set_smem(mg0_up_kernel<NU>, sm);
+  cudaError_t e = set_smem<mg0_up_kernel<NU>>(sm);
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg0_up", st); mg0_up_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  { LaunchScope ls_("mg0_up", st); mg0_up_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
   return cudaGetLastError();
 }
 
 template <int NU>
 cudaError_t launch_mg_down(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
   const size_t sm = LvDownShape<NU>::smem;
-  cudaError_t e = set_smem(mg_down_kernel<NU>, sm);
+  cudaError_t e = set_smem<mg_down_kernel<NU>>(sm);
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg_down", st); mg_down_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k, first); }
+  { LaunchScope ls_("mg_down", st); mg_down_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k, first); }
   return cudaGetLastError();
 }
 
 template <int NU>
 cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
   const size_t sm = LvUpShape<NU>::smem;
-  cudaError_t e = set_smem(mg_up_kernel<NU>, sm);
+  cudaError_t e = set_smem<mg_up_kernel<NU>>(sm);
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg_up", st); mg_up_kernel<NU><<<grid, kMgThreads, sm, st>>>(a, ctrl, k); }
+  { LaunchScope ls_("mg_up", st); mg_up_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
   return cudaGetLastError();
 }
 
 template <int NU1, int NU2>
 cudaError_t launch_tail_t(const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int first, int C,
                           cudaStream_t st) {
-  cudaError_t e = set_smem(mg_tail_kernel<NU1, NU2>, sm);
+  cudaError_t e = set_smem<mg_tail_kernel<NU1, NU2>>(sm);
   if (e != cudaSuccess) return e;
-  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, kTailThreads, sm, st>>>(a, ctrl, k, first); }
+  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, dim3(32, 32), sm, st>>>(a, ctrl, k, first); }
   return cudaGetLastError();
 }
 
@@ -808,10 +953,182 @@ cudaError_t launch_tail(int nu1, int nu2, const TailArgs &a, size_t sm, Ctrl *ct
   return cudaErrorInvalidValue;
 }
 
-#define GDGS_NU_DISPATCH(NU, CALL) \
-  ((NU) == 1 ? CALL<1> : (NU) == 2 ? CALL<2> : CALL<3>)
+// Everything one V-cycle launches, for workspace `ws` laid out by `p`.
+struct Cycle {
+  const Plan *p;
+  char *ws;
+  Ctrl *ctrl;
+  int C, nu1, nu2;
+  L0Args l0;
+  TailArgs ta;
+  size_t tail_smem;
+
+  LvArgs level(int l) const {
+    return LvArgs{p->lv[l], p->lv[l + 1], (float *)(ws + p->off_lf[l]), (float *)(ws + p->off_lu[l]),
+                  (float *)(ws + p->off_lf[l + 1]), (const float *)(ws + p->off_lu[l + 1])};
+  }
+  unsigned kernels() const { return 2u * (unsigned)p->tail + 2u; }
+
+  // Opt-in to large dynamic shared memory for every kernel of the cycle; done
+  // before any capture (attributes are set once per kernel and device).
+  template <int A, int B>
+  cudaError_t prepare_t() const {
+    cudaError_t e = set_smem<mg0_down_kernel<A>>(L0DownShape<A>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_down_kernel<A>>(LvDownShape<A>::smem);
+    if (e == cudaSuccess) e = set_smem<mg0_up_kernel<B>>(L0UpShape<B>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_up_kernel<B>>(LvUpShape<B>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_tail_kernel<A, B>>(tail_smem);
+    return e;
+  }
+  cudaError_t prepare() const {
+#define GDGS_PREP(A, B) \
+  if (nu1 == A && nu2 == B) return prepare_t<A, B>();
+    GDGS_PREP(1, 1) GDGS_PREP(1, 2) GDGS_PREP(1, 3)
+    GDGS_PREP(2, 1) GDGS_PREP(2, 2) GDGS_PREP(2, 3)
+    GDGS_PREP(3, 1) GDGS_PREP(3, 2) GDGS_PREP(3, 3)
+#undef GDGS_PREP
+    return cudaErrorInvalidValue;
+  }
+
+  // k >= 0: explicit cycle index; k < 0: read from ctrl->iter (graph body).
+  cudaError_t launch(int k, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) const {
+    cudaError_t e = nu1 == 1 ? launch_mg0_down<1>(l0, ctrl, k, C, st)
+                    : nu1 == 2 ? launch_mg0_down<2>(l0, ctrl, k, C, st)
+                               : launch_mg0_down<3>(l0, ctrl, k, C, st);
+    if (e != cudaSuccess) return e;
+    for (int l = 1; l < p->tail; ++l) {
+      const LvArgs la = level(l);
+      const int first = (l == 1);
+      e = nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, C, st)
+          : nu1 == 2 ? launch_mg_down<2>(la, ctrl, k, first, C, st)
+                     : launch_mg_down<3>(la, ctrl, k, first, C, st);
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_tail(nu1, nu2, ta, tail_smem, ctrl, k, p->tail == 1 ? 1 : 0, C, st);
+    if (e != cudaSuccess) return e;
+    for (int l = p->tail - 1; l >= 1; --l) {
+      const LvArgs la = level(l);
+      e = nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, C, st)
+          : nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, C, st)
+                     : launch_mg_up<3>(la, ctrl, k, C, st);
+      if (e != cudaSuccess) return e;
+    }
+    e = nu2 == 1 ? launch_mg0_up<1>(l0, ctrl, k, C, st)
+        : nu2 == 2 ? launch_mg0_up<2>(l0, ctrl, k, C, st)
+                   : launch_mg0_up<3>(l0, ctrl, k, C, st);
+    if (e != cudaSuccess) return e;
+    {
+      LaunchScope ls_("mg_advance", st);
+      advance_kernel<<<1, 1, 0, st>>>(ctrl, k, h, in_graph, kernels());
+    }
+    return cudaGetLastError();
+  }
+};
+
+// ---- graph executor: the cycle loop as a CUDA graph with a WHILE node whose
+// body is one V-cycle; the advance kernel ends the loop on convergence, so no
+// launch is spent after it. Kernel parameters reference the workspace only, so
+// one graph serves every call on the same workspace, shape and options.
+
+struct GraphKey {
+  int dev;
+  const void *ws;
+  int C, H, W, nu1, nu2, max_cycles, coarse;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, coarse) <
+           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.coarse);
+  }
+};
+
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long last_use = 0;
+};
+
+std::mutex g_graph_mu;
+std::map<GraphKey, GraphEntry> g_graphs;
+unsigned long long g_graph_clock = 0;
+constexpr size_t kMaxGraphs = 64;
+
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("GDGS_GRAPHS");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+cudaError_t build_cycle_graph(const Cycle &cy, GraphEntry *out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  cudaStream_t cs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      diag_set_capturing(true);
+      const cudaError_t le = cy.launch(-1, h, 1, cs);
+      diag_set_capturing(false);
+      e = cudaStreamEndCapture(cs, &body);
+      if (le != cudaSuccess) e = le;
+    }
+  }
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  out->graph = g;
+  out->exec = x;
+  return cudaSuccess;
+}
+
+cudaError_t launch_cycle_graph(const Cycle &cy, const GraphKey &key, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  auto it = g_graphs.find(key);
+  if (it == g_graphs.end()) {
+    if (g_graphs.size() >= kMaxGraphs) {  // evict the least recently used
+      auto lru = g_graphs.begin();
+      for (auto jt = g_graphs.begin(); jt != g_graphs.end(); ++jt)
+        if (jt->second.last_use < lru->second.last_use) lru = jt;
+      cudaDeviceSynchronize();
+      cudaGraphExecDestroy(lru->second.exec);
+      cudaGraphDestroy(lru->second.graph);
+      g_graphs.erase(lru);
+    }
+    GraphEntry ent;
+    cudaError_t e = build_cycle_graph(cy, &ent);
+    if (e != cudaSuccess) return e;
+    it = g_graphs.emplace(key, ent).first;
+  }
+  it->second.last_use = ++g_graph_clock;
+  return cudaGraphLaunch(it->second.exec, st);
+}
 
 }  // namespace
+
+unsigned long long graph_kernel_count() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_graph_kernels, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
+}
 
 cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   const Plan &p = *a.plan;
@@ -848,58 +1165,48 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   { LaunchScope ls_("coarse_setup", st); coarse_setup_kernel<<<1, 1024, 0, st>>>(gcoarse, Minv, tag, want); }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  L0Args l0{p.lv[0], p.lv[1], rho, uhi, ulo, e0, (float *)(ws + p.off_lf[1]),
-            (const float *)(ws + p.off_lu[1])};
-  TailArgs ta{};
-  ta.lt = p.tail;
-  ta.L = p.levels - 1;
+  Cycle cy{};
+  cy.p = &p;
+  cy.ws = ws;
+  cy.ctrl = ctrl;
+  cy.C = a.C;
+  cy.nu1 = a.nu1;
+  cy.nu2 = a.nu2;
+  cy.l0 = L0Args{p.lv[0], p.lv[1], rho, uhi, ulo, e0, (float *)(ws + p.off_lf[1]),
+                 (const float *)(ws + p.off_lu[1])};
+  cy.ta.lt = p.tail;
+  cy.ta.L = p.levels - 1;
   int off = 0;
   for (int l = 0; l < p.levels; ++l) {
-    ta.g[l] = p.lv[l];
+    cy.ta.g[l] = p.lv[l];
     if (l >= p.tail) {
-      ta.off[l] = off;
+      cy.ta.off[l] = off;
       off += 2 * p.lv[l].H * p.lv[l].W;
     }
   }
-  const size_t tail_smem = (size_t)off * sizeof(float);
-  ta.f_lt = (const float *)(ws + p.off_lf[p.tail]);
-  ta.u_lt = (float *)(ws + p.off_lu[p.tail]);
-  ta.Minv = Minv;
-  ta.nc = p.nc;
+  cy.tail_smem = (size_t)off * sizeof(float);
+  cy.ta.f_lt = (const float *)(ws + p.off_lf[p.tail]);
+  cy.ta.u_lt = (float *)(ws + p.off_lu[p.tail]);
+  cy.ta.Minv = Minv;
+  cy.ta.nc = p.nc;
 
-  for (int k = 0; k < a.max_cycles; ++k) {
-    e = a.nu1 == 1 ? launch_mg0_down<1>(l0, ctrl, k, a.C, st)
-        : a.nu1 == 2 ? launch_mg0_down<2>(l0, ctrl, k, a.C, st)
-                     : launch_mg0_down<3>(l0, ctrl, k, a.C, st);
-    if (e != cudaSuccess) return e;
-    for (int l = 1; l < p.tail; ++l) {
-      LvArgs la{p.lv[l], p.lv[l + 1], (float *)(ws + p.off_lf[l]), (float *)(ws + p.off_lu[l]),
-                (float *)(ws + p.off_lf[l + 1]), (const float *)(ws + p.off_lu[l + 1])};
-      const int first = (l == 1);
-      e = a.nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, a.C, st)
-          : a.nu1 == 2 ? launch_mg_down<2>(la, ctrl, k, first, a.C, st)
-                       : launch_mg_down<3>(la, ctrl, k, first, a.C, st);
-      if (e != cudaSuccess) return e;
-    }
-    e = launch_tail(a.nu1, a.nu2, ta, tail_smem, ctrl, k, p.tail == 1 ? 1 : 0, a.C, st);
-    if (e != cudaSuccess) return e;
-    for (int l = p.tail - 1; l >= 1; --l) {
-      LvArgs la{p.lv[l], p.lv[l + 1], (float *)(ws + p.off_lf[l]), (float *)(ws + p.off_lu[l]),
-                (float *)(ws + p.off_lf[l + 1]), (const float *)(ws + p.off_lu[l + 1])};
-      e = a.nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, a.C, st)
-          : a.nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, a.C, st)
-                       : launch_mg_up<3>(la, ctrl, k, a.C, st);
-      if (e != cudaSuccess) return e;
-    }
-    e = a.nu2 == 1 ? launch_mg0_up<1>(l0, ctrl, k, a.C, st)
-        : a.nu2 == 2 ? launch_mg0_up<2>(l0, ctrl, k, a.C, st)
-                     : launch_mg0_up<3>(l0, ctrl, k, a.C, st);
-    if (e != cudaSuccess) return e;
+  if ((e = cy.prepare()) != cudaSuccess) return e;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const GraphKey key{dev, ws, a.C, a.H, a.W, a.nu1, a.nu2, a.max_cycles, p.levels};
+    if ((e = launch_cycle_graph(cy, key, st)) != cudaSuccess) return e;
+  } else {
+    // direct launches: every cycle is enqueued; once the advance kernel has
+    // recorded convergence the remaining ones return at their first check
+    for (int k = 0; k < a.max_cycles; ++k)
+      if ((e = cy.launch(k, 0, 0, st)) != cudaSuccess) return e;
   }
 
   FinArgs fa{};
   fa.g0 = p.lv[0];
-  fa.rho = rho;
   fa.uhi = uhi;
   fa.ulo = ulo;
   fa.image = a.image;

@@ -285,3 +285,28 @@ def test_render_view_workspace_too_small_raises():
     with pytest.raises(G.GDGSError) as e:
         _render(scene, cam, mean, nbytes=4096)
     assert e.value.code == G._abi.ERR_WORKSPACE
+
+
+def test_graph_and_direct_cycle_loops_agree():
+    """The cycle loop launched as a CUDA graph (WHILE node, default) and as direct
+    launches (used while profiling) give bit-identical images and cycle counts."""
+    scene, cam = _small_prims(n=8000)
+    mean = [0.5, 0.5, 0.5]
+    a, sa = _render(scene, cam, mean)
+    G.profile_begin()
+    b, sb = _render(scene, cam, mean)
+    prof = G.profile_end()
+    assert "mg0_up" in prof and prof["mg0_up"][0] >= sb["cycles"]
+    assert sa["status"] == sb["status"] == 0
+    assert sa["cycles"] == sb["cycles"]
+    assert np.array_equal(a, b)
+
+
+def test_kernel_launch_count_covers_graph_kernels():
+    scene, cam, mean, _ = S.workload("tiny64")
+    _render(scene, cam, mean)  # warm: builds the cycle graph for this shape
+    n0 = G.kernel_launch_count()
+    img, st = _render(scene, cam, mean)
+    n1 = G.kernel_launch_count()
+    # projection, sorts, raster, divergence, setup, finalize + per cycle kernels
+    assert n1 - n0 >= 10 + 4 * st["cycles"]
