@@ -1030,13 +1030,18 @@ struct Cycle {
 // launch is spent after it. Kernel parameters reference the workspace only, so
 // one graph serves every call on the same workspace, shape and options.
 
+// The key pins every pointer the graph bakes in: the workspace base and the
+// layout of the solver's regions inside it (which depends on n and the pair
+// capacity as well as on the image shape).
 struct GraphKey {
   int dev;
   const void *ws;
-  int C, H, W, nu1, nu2, max_cycles, coarse;
+  int C, H, W, nu1, nu2, max_cycles, levels;
+  size_t off_rho, off_coarse, total;
   bool operator<(const GraphKey &o) const {
-    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, coarse) <
-           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.coarse);
+    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, off_rho, off_coarse, total) <
+           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.levels, o.off_rho,
+                    o.off_coarse, o.total);
   }
 };
 
@@ -1196,7 +1201,8 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const GraphKey key{dev, ws, a.C, a.H, a.W, a.nu1, a.nu2, a.max_cycles, p.levels};
+    const GraphKey key{dev, ws, a.C, a.H, a.W, a.nu1, a.nu2, a.max_cycles, p.levels,
+                       p.off_rho, p.off_coarse, p.total};
     if ((e = launch_cycle_graph(cy, key, st)) != cudaSuccess) return e;
   } else {
     // direct launches: every cycle is enqueued; once the advance kernel has

@@ -310,3 +310,26 @@ def test_kernel_launch_count_covers_graph_kernels():
     n1 = G.kernel_launch_count()
     # projection, sorts, raster, divergence, setup, finalize + per cycle kernels
     assert n1 - n0 >= 10 + 4 * st["cycles"]
+
+
+def test_graph_cache_distinguishes_workspace_layouts():
+    """A Poisson-only workspace and a render workspace of the same image size have
+    different layouts; reusing one address for both must not reuse a stale graph."""
+    scene, cam = _small_prims(n=3000, w=200, h=120)
+    mean = [0.5, 0.5, 0.5]
+    C, H, W = 3, cam.height, cam.width
+    big = G.workspace_size(scene.n, C, W, H, None, None)
+    ws = torch.empty(big, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(4)
+    maps = torch.as_tensor(rng.laplace(0, 0.1, (C, 2, H, W)).astype(np.float32)).cuda()
+    img = torch.empty((C, H, W), device="cuda")
+    small = ws[:G.workspace_size(0, C, W, H, None, None)]
+    G.poisson_reconstruct(maps, mean, img, small)  # builds a graph for the Poisson-only layout
+    assert G.sync_status(small)["status"] == 0
+    g = G.gaussians_to_device(scene)
+    G.render_view(g, cam, mean, img, ws)  # same base address, render layout
+    st = G.sync_status(ws)
+    assert st["status"] == 0
+    ref, _, _ = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
+    assert np.isfinite(img.cpu().numpy()).all()
+    assert img_err(img.cpu().numpy().astype(np.float64), ref)[1] <= IMG_TOL
