@@ -91,20 +91,40 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def mg_levels(H: int, W: int, coarse_max: int = 16, tail_budget: int = 8 * 1024):
+    """Level sizes of the solver (ceil halving until both sides <= coarse_max, at
+    least two levels) and the first level run by the single-CTA tail."""
+    lv = [(H, W)]
+    while len(lv) < 2 or max(lv[-1]) > coarse_max:
+        h, w = lv[-1]
+        lv.append(((h + 1) // 2, (w + 1) // 2))
+    tail, used = len(lv) - 1, 2 * 4 * lv[-1][0] * lv[-1][1]
+    for l in range(len(lv) - 2, 0, -1):
+        b = 2 * 4 * lv[l][0] * lv[l][1]
+        if used + b > tail_budget:
+            break
+        used, tail = used + b, l
+    return lv, tail
+
+
 def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,
                       n_pairs: int) -> float:
-    """Bytes each kernel must move per view (ideal single pass, no re-reads)."""
+    """Bytes each kernel must move per view (one pass over its inputs and outputs)."""
     px = C * H * W
-    if kernel == "mg0_down":   # k = 0: rho in, e0 + f1 out; k > 0: also u (hi, lo) in
-        return px * (4 + 4 + 1) + cycles * px * 8
-    if kernel == "mg0_up":     # e0, rho, coarse e1 in, u (hi, lo) out; k > 0: u in
-        return cycles * px * (4 + 4 + 1 + 8) + max(cycles - 1, 0) * px * 8
-    if kernel == "divergence":
+    lv, tail = mg_levels(H, W)
+    if kernel == "mg0_down":   # r_k in; e, coarse rhs out
+        return cycles * px * (4 + 4 + 1)
+    if kernel == "mg0_up":     # r_k, e, coarse e in; u (hi, lo) out, r_{k+1} out; u in for k > 0
+        return cycles * px * (4 + 4 + 1 + 8 + 4) + max(cycles - 1, 0) * px * 8
+    if kernel in ("mg_down", "mg_up"):  # levels 1 .. tail-1
+        per = 4 + 4 + 1 if kernel == "mg_down" else 4 + 4 + 1 + 4
+        return cycles * sum(per * C * h * w for h, w in lv[1:tail])
+    if kernel == "divergence":  # maps in, rho out
         return px * (8 + 4)
-    if kernel == "finalize":
-        return px * (8 + 4)
-    if kernel == "raster":     # splat records + index per pair, maps out
-        return n_pairs * (4 + 32 + 8 * C) / 1.0 + px * 8
+    if kernel == "finalize":    # rho, u in; image out
+        return px * (4 + 8 + 4)
+    if kernel == "raster":      # per pair: index + splat record + attribute; maps out
+        return n_pairs * (4 + 32 + 8 * C) + px * 8
     if kernel == "project":
         return n_gauss * (4 * (3 + 3 + 4 + 1 + 2 * C) + 16 + 16 + 4 + 8)
     return 0.0
@@ -286,13 +306,18 @@ def main():
                                                             st["n_pairs"]) > 0 and k != "raster"]
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     roof_k = dom if dom in hbm_kernels else max(hbm_kernels, key=lambda k: kernels[k]["share"])
+    per_kernel_roof = {}
+    for k in hbm_kernels:
+        b_ = algorithmic_bytes(k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
+        per_kernel_roof[k] = round(b_ / (kernels[k]["ms_per_view"] / 1e3) / 1e9 / hbm, 4)
     nbytes = algorithmic_bytes(roof_k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
     ms = kernels[roof_k]["ms_per_view"]
     achieved = nbytes / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": roof_k, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
                 "algorithmic_bytes_per_view": nbytes, "traffic": None,
-                "dominant_kernel": dom, "dominant_share": kernels[dom]["share"]}
+                "dominant_kernel": dom, "dominant_share": kernels[dom]["share"],
+                "frac_by_kernel": per_kernel_roof}
 
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,

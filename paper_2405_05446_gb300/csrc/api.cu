@@ -10,7 +10,7 @@ namespace gdgs {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kTailSmemBudget = 160 * 1024;
+constexpr size_t kTailSmemBudget = 8 * 1024;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -122,6 +122,8 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
   p->off_uhi = cv.take(plane0);
   p->off_ulo = cv.take(plane0);
   p->off_e0 = cv.take(plane0);
+  p->off_r[0] = cv.take(plane0);
+  p->off_r[1] = cv.take(plane0);
   for (int l = 1; l < levels; ++l) {
     const size_t b = sizeof(float) * (size_t)C * p->lv[l].plane;
     p->off_lu[l] = cv.take(b);
@@ -465,8 +467,7 @@ int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream) {
   double rel = 0.0;
   if (c.max_cycles > 0) {  // a solve ran
     const double r0 = c.rnorm2[0];
-    const int kf = c.cycles < 0 ? 0 : (c.cycles > kMaxCycles ? kMaxCycles : c.cycles);
-    rel = r0 > 0 ? sqrt(c.rnorm2[kf] / r0) : 0.0;
+    rel = r0 > 0 ? sqrt(c.final_rnorm2 / r0) : 0.0;
     if (status == GDGS_OK && !c.stopped && rel > c.rtol) status = GDGS_ERR_NO_CONVERGE;
   }
   if (stats) {

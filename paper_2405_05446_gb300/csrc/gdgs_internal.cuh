@@ -84,7 +84,7 @@ struct Plan {
   size_t off_pkey[2], off_pval[2];                     // pairs [pair_cap]
   size_t off_range, off_active, off_mask;              // per tile
   size_t off_maps;                                     // [C][2][H][W]
-  size_t off_rho, off_uhi, off_ulo, off_e0;            // level 0 [C][H][W]
+  size_t off_rho, off_uhi, off_ulo, off_e0, off_r[2];  // level 0 [C][H][W]
   size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1
   size_t off_coarse;                                   // tag + FP64 inverse
   int levels;         // number of levels (finest = 0, coarsest = levels-1)

@@ -19,24 +19,28 @@
 // zero-mean solution of L u = f), built once per grid shape by Gauss-Jordan on
 // the device and cached in the workspace under a tag.
 //
-// Smoother and blocking. Red-black Gauss-Seidel. On the large levels one CTA
-// owns a 32x64 output tile, loads it with a halo of 2 nu + 1 cells into shared
-// memory and runs all nu sweeps there (each half-sweep shrinks the valid region
-// by one cell), then fuses the residual with the 2x2 restriction (down) or the
-// prolongation with the post-sweeps (up). Levels that fit in shared memory are
-// handled by one CTA per channel that runs the rest of the V-cycle in place.
+// Iteration. The finest iterate u is a float-float pair (hi + lo): an FP32
+// image carries a representation error that alone gives a relative residual
+// ~1e-5 on 1080p scenes, above the 1e-6 target. Cycle k solves L e = r_k with an
+// FP32 V(nu1, nu2)-cycle from e = 0, then u += e with an error-free sum and
+// r_{k+1} = r_k - L e (r_0 = rho), whose norm decides convergence on the device.
+// The final iterate's residual rho - L u is recomputed in float-float arithmetic.
 //
-// Precision. An FP32 image carries a representation error that alone gives a
-// relative residual ~1e-5 on 1080p scenes, above the 1e-6 target. The finest
-// iterate is therefore kept as a float-float pair (hi + lo) and refined:
-// each cycle computes r = rho - L u in float-float arithmetic, runs the FP32
-// V-cycle on L e = r from e = 0, and adds e to u with an error-free sum. Every
-// coarser level works on FP32 corrections.
+// Smoother and blocking. Red-black Gauss-Seidel. A CTA owns a 32 x 128 output
+// tile of a level, loads it with a halo of 2 nu + 1 rows (rounded up to 4 in x)
+// into shared memory and runs all sweeps there: every half-sweep shrinks the
+// valid region by one cell, and the halo absorbs that. Shared memory keeps the
+// even-x and odd-x cells of each row in separate planes, so the cells of one
+// colour in a row are contiguous and a half-sweep updates them four at a time
+// with 16-byte loads; work units away from the grid border take that path, the
+// few at the border a scalar path with the exact boundary coefficients. Down
+// kernels fuse the pre-sweeps with residual and restriction, up kernels the
+// prolongation with the post-sweeps (and, on the finest level, the update of u,
+// the new residual and its norm). Levels that fit in shared memory run the rest
+// of the V-cycle inside one CTA per channel.
 //
-// Convergence is decided on the device: the finest "down" kernel of cycle k
-// accumulates ||rho - L u_k||^2; every later kernel of that cycle returns at
-// once when it is <= rtol^2 ||rho||^2, and the first one records the stop, so the
-// remaining launches of the cycle loop do no work.
+// Convergence is decided on the device, so the cycle loop runs as a CUDA graph
+// with a WHILE node: no launch is spent after convergence.
 #include <stdlib.h>
 
 #include <atomic>
@@ -50,9 +54,14 @@ namespace gdgs {
 
 namespace {
 
-constexpr int TY = 32, TX = 64;  // output tile of the shared-memory level kernels
-constexpr int kMgThreads = 256;
-constexpr int kTailThreads = 1024;
+constexpr int kBX = 32, kBY = 8;     // 256 threads
+constexpr int kMgThreads = kBX * kBY;
+constexpr int kTailBY = 8;           // tail CTA: 32 x 8 threads
+constexpr int kTailThreads = 32 * kTailBY;
+// Output tiles of the level kernels: large levels use 32 x 128 cells, levels
+// with fewer cells per channel than kSmallLevel 16 x 64 (more CTAs, shorter
+// serial work per CTA, which is what bounds the small grids).
+constexpr long long kSmallLevel = 160000;
 
 // ------------------------------------------------------------------ operator
 
@@ -74,8 +83,13 @@ __device__ __forceinline__ Coef coef(const LevelGeom &g, int I, int J) {
   return c;
 }
 
+// All four face coefficients are 1 (full cell, full neighbours).
 __device__ __forceinline__ bool interior(const LevelGeom &g, int I, int J) {
   return I > 0 && J > 0 && I < g.H - 2 && J < g.W - 2;
+}
+
+__device__ __forceinline__ bool in_grid(const LevelGeom &g, int I, int J) {
+  return I >= 0 && J >= 0 && I < g.H && J < g.W;
 }
 
 __device__ __forceinline__ float gs_value(const LevelGeom &g, int I, int J, float uE, float uW,
@@ -86,9 +100,11 @@ __device__ __forceinline__ float gs_value(const LevelGeom &g, int I, int J, floa
   return d > 0.f ? (c.e * uE + c.w * uW + c.s * uS + c.n * uN - f) / d : 0.f;
 }
 
+// Differences to the centre keep the rounding relative to L u, not to u: a
+// correction as large as the image itself still gets an accurate residual.
 __device__ __forceinline__ float residual(const LevelGeom &g, int I, int J, float u, float uE,
                                           float uW, float uS, float uN, float f) {
-  if (interior(g, I, J)) return f - ((uE + uW) + (uS + uN) - 4.f * u);
+  if (interior(g, I, J)) return f - (((uE - u) + (uW - u)) + ((uS - u) + (uN - u)));
   const Coef c = coef(g, I, J);
   return f - (c.e * (uE - u) + c.w * (uW - u) + c.s * (uS - u) + c.n * (uN - u));
 }
@@ -131,7 +147,8 @@ __device__ __forceinline__ bool should_stop(Ctrl *ctrl, int k, int first) {
   if (*(volatile int *)&ctrl->stopped) return true;
   const double thr = ctrl->rtol * ctrl->rtol * ctrl->rnorm2[0];
   if (ctrl->rnorm2[k] <= thr) {
-    if (first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+    if (first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0) {
       ctrl->stopped = 1;
       ctrl->cycles = k;
     }
@@ -157,328 +174,392 @@ __device__ float block_sum(float v) {
   return s;
 }
 
-// ------------------------------------------------------------------ region helpers
-//
-// Shared-memory region kernels run 256 threads as a 32 x 8 grid (tx, ty). A
-// region has RY x RX cells with origin (ry0, rx0) in level coordinates; rows are
-// walked with stride 8 and columns with stride 32, so every trip count is a
-// compile-time constant. INT marks a block whose whole region lies two cells or
-// more inside the grid: there every face coefficient is 1 and no bounds test is
-// needed.
-
-constexpr int kBX = 32, kBY = 8;
-
-template <int RY, int RX>
-__device__ __forceinline__ bool region_interior(const LevelGeom &g, int ry0, int rx0) {
-  return ry0 >= 1 && rx0 >= 1 && ry0 + RY - 1 <= g.H - 3 && rx0 + RX - 1 <= g.W - 3;
-}
-
-// One red-black half-sweep over the cells of colour `col` at least `s` cells
-// inside the region (and inside the grid).
-template <int RY, int RX, bool INT>
-__device__ __forceinline__ void half_sweep(float *U, const float *F, const LevelGeom &g, int ry0,
-                                           int rx0, int s, int col) {
-  for (int yy = s + threadIdx.y; yy < RY - s; yy += kBY) {
-    const int gy = ry0 + yy;
-    const int x0 = s + (((gy + rx0 + s) ^ col) & 1);
-#pragma unroll
-    for (int j = 0; j < (RX + 2 * kBX - 1) / (2 * kBX); ++j) {
-      const int xx = x0 + 2 * (threadIdx.x + kBX * j);
-      if (xx < RX - s) {
-        const int o = yy * RX + xx;
-        if (INT) {
-          U[o] = 0.25f * ((U[o + 1] + U[o - 1]) + (U[o + RX] + U[o - RX]) - F[o]);
-        } else {
-          const int gx = rx0 + xx;
-          if (gy >= 0 && gy < g.H && gx >= 0 && gx < g.W)
-            U[o] = gs_value(g, gy, gx, U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
-        }
-      }
-    }
-  }
-}
-
-template <int RY, int RX>
-__device__ __forceinline__ void load_region(float *dst, const float *__restrict__ src,
-                                            const LevelGeom &g, int ry0, int rx0) {
-  for (int yy = threadIdx.y; yy < RY; yy += kBY) {
-    const int gy = ry0 + yy;
-    const bool rin = gy >= 0 && gy < g.H;
-    for (int xx = threadIdx.x; xx < RX; xx += kBX) {
-      const int gx = rx0 + xx;
-      dst[yy * RX + xx] = (rin && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) : 0.f;
-    }
-  }
-}
-
-template <int RY, int RX>
-__device__ __forceinline__ void zero_region(float *dst) {
-  for (int yy = threadIdx.y; yy < RY; yy += kBY)
-    for (int xx = threadIdx.x; xx < RX; xx += kBX) dst[yy * RX + xx] = 0.f;
-}
-
-// R = rho - L u on the cells one or more inside the region, u = hi + lo read
-// through the read-only cache; R must already hold rho. Float-float sums keep
-// the residual of an iterate whose FP32 rounding alone would exceed the target.
-template <int RY, int RX, bool INT>
-__device__ __forceinline__ void residual_ds(float *R, const float *__restrict__ uhi,
-                                            const float *__restrict__ ulo, const LevelGeom &g,
-                                            int ry0, int rx0) {
-  for (int yy = 1 + threadIdx.y; yy < RY - 1; yy += kBY) {
-    const int gy = ry0 + yy;
-    for (int xx = 1 + threadIdx.x; xx < RX - 1; xx += kBX) {
-      const int gx = rx0 + xx;
-      if (!INT && (gy < 0 || gy >= g.H || gx < 0 || gx >= g.W)) continue;
-      const size_t p = (size_t)gy * g.W + gx;
-      const float hi = __ldg(uhi + p), lo = __ldg(ulo + p);
-      float sh, sl;
-      if (INT) {
-        sh = ((__ldg(uhi + p + 1) - hi) + (__ldg(uhi + p - 1) - hi)) +
-             ((__ldg(uhi + p + g.W) - hi) + (__ldg(uhi + p - g.W) - hi));
-        sl = ((__ldg(ulo + p + 1) - lo) + (__ldg(ulo + p - 1) - lo)) +
-             ((__ldg(ulo + p + g.W) - lo) + (__ldg(ulo + p - g.W) - lo));
-      } else {
-        sh = 0.f;
-        sl = 0.f;
-        if (gx + 1 < g.W) { sh += __ldg(uhi + p + 1) - hi; sl += __ldg(ulo + p + 1) - lo; }
-        if (gx > 0) { sh += __ldg(uhi + p - 1) - hi; sl += __ldg(ulo + p - 1) - lo; }
-        if (gy + 1 < g.H) { sh += __ldg(uhi + p + g.W) - hi; sl += __ldg(ulo + p + g.W) - lo; }
-        if (gy > 0) { sh += __ldg(uhi + p - g.W) - hi; sl += __ldg(ulo + p - g.W) - lo; }
-      }
-      const int o = yy * RX + xx;
-      R[o] = R[o] - (sh + sl);
-    }
-  }
-}
-
-// Residual of (U, F) on the four children of each coarse cell under the output
-// tile, summed into the coarse right-hand side. Thread (tx, ty) owns coarse
-// column tx and rows ty, ty + 8.
-template <int RY, int RX, int HALO, bool INT>
-__device__ __forceinline__ void restrict_tile(const float *U, const float *F, const LevelGeom &g,
-                                              const LevelGeom &gc, int ty0, int tx0, float *fc) {
-  const int ry0 = ty0 - HALO, rx0 = tx0 - HALO;
-  const int CJ = (tx0 >> 1) + threadIdx.x;
-#pragma unroll
-  for (int i = 0; i < TY / 2 / kBY; ++i) {
-    const int CI = (ty0 >> 1) + threadIdx.y + kBY * i;
-    if (CI >= gc.H || CJ >= gc.W) continue;
-    float sum = 0.f;
-#pragma unroll
-    for (int di = 0; di < 2; ++di)
-#pragma unroll
-      for (int dj = 0; dj < 2; ++dj) {
-        const int gy = 2 * CI + di, gx = 2 * CJ + dj;
-        const int o = (gy - ry0) * RX + (gx - rx0);
-        if (INT) {
-          sum += F[o] - ((U[o + 1] + U[o - 1]) + (U[o + RX] + U[o - RX]) - 4.f * U[o]);
-        } else if (gy < g.H && gx < g.W) {
-          sum += residual(g, gy, gx, U[o], U[o + 1], U[o - 1], U[o + RX], U[o - RX], F[o]);
-        }
-      }
-    fc[(size_t)CI * gc.W + CJ] = sum;
-  }
-}
-
-// Coarse region that covers the prolongation stencils of a fine region.
-struct CoarseBox {
-  int cy0, cx0, CRY, CRX;
-};
-
-__device__ __forceinline__ CoarseBox coarse_box(int ry0, int rx0, int RY, int RX) {
-  CoarseBox b;
-  b.cy0 = (ry0 >> 1) - 1;
-  b.cx0 = (rx0 >> 1) - 1;
-  b.CRY = ((ry0 + RY - 1) >> 1) + 1 - b.cy0 + 1;
-  b.CRX = ((rx0 + RX - 1) >> 1) + 1 - b.cx0 + 1;
-  return b;
-}
-
-__device__ __forceinline__ void load_coarse(float *EC, const float *__restrict__ uc,
-                                            const LevelGeom &gc, const CoarseBox &b) {
-  for (int yy = threadIdx.y; yy < b.CRY; yy += kBY) {
-    const int gy = b.cy0 + yy;
-    const bool rin = gy >= 0 && gy < gc.H;
-    for (int xx = threadIdx.x; xx < b.CRX; xx += kBX) {
-      const int gx = b.cx0 + xx;
-      EC[yy * b.CRX + xx] = (rin && gx >= 0 && gx < gc.W) ? __ldg(uc + (size_t)gy * gc.W + gx) : 0.f;
-    }
-  }
-}
-
-// U += P(EC) on every in-grid cell of the region; column weights are computed
-// once per thread, row weights once per row.
-template <int RY, int RX>
-__device__ __forceinline__ void prolong_region(float *U, const float *EC, const LevelGeom &g,
-                                               const LevelGeom &gc, const CoarseBox &b, int ry0,
-                                               int rx0) {
-  constexpr int NJ = (RX + kBX - 1) / kBX;
-  int j0[NJ], j1[NJ];
-  float wx[NJ];
-  bool cin[NJ];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int xx = threadIdx.x + kBX * j;
-    const int gx = rx0 + xx;
-    cin[j] = xx < RX && gx >= 0 && gx < g.W;
-    const P1 px = prolong1d(cin[j] ? gx : 0, g.shift, g.W0, gc.W);
-    j0[j] = px.i0 - b.cx0;
-    j1[j] = px.i1 - b.cx0;
-    wx[j] = px.w1;
-  }
-  for (int yy = threadIdx.y; yy < RY; yy += kBY) {
-    const int gy = ry0 + yy;
-    if (gy < 0 || gy >= g.H) continue;
-    const P1 py = prolong1d(gy, g.shift, g.H0, gc.H);
-    const float *r0 = EC + (py.i0 - b.cy0) * b.CRX;
-    const float *r1 = EC + (py.i1 - b.cy0) * b.CRX;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (!cin[j]) continue;
-      const float a0 = r0[j0[j]] + wx[j] * (r0[j1[j]] - r0[j0[j]]);
-      const float a1 = r1[j0[j]] + wx[j] * (r1[j1[j]] - r1[j0[j]]);
-      U[yy * RX + threadIdx.x + kBX * j] += a0 + py.w1 * (a1 - a0);
-    }
-  }
-}
-
-// ------------------------------------------------------------------ kernels
-
-struct L0Args {
-  LevelGeom g0, g1;
-  const float *rho;
-  float *uhi, *ulo, *e0;
-  float *f1;        // level-1 right-hand side (down)
-  const float *u1;  // level-1 correction (up)
-};
-
-template <int NU>
-struct L0DownShape {
-  static constexpr int H = 2 * NU + 1;
-  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
-  static constexpr size_t smem = 2 * RN * sizeof(float);
-};
-
 __device__ __forceinline__ int cycle_index(const Ctrl *ctrl, int k) { return k >= 0 ? k : ctrl->iter; }
 
-// Finest level, first half of a cycle: r_k = rho - L u_k in float-float, its
-// norm, nu1 sweeps on L e = r_k from e = 0, then restriction of r_k - L e.
-template <int NU, bool INT>
-__device__ __forceinline__ void mg0_down_body(const L0Args &a, Ctrl *ctrl, int k, float *R, float *E) {
-  using S = L0DownShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX;
-  const LevelGeom &g = a.g0;
-  const int c = blockIdx.z;
-  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
-  const int ry0 = ty0 - H, rx0 = tx0 - H;
-  const size_t cb = (size_t)c * g.plane;
-  load_region<RY, RX>(R, a.rho + cb, g, ry0, rx0);
-  zero_region<RY, RX>(E);
-  __syncthreads();
-  if (k > 0) {
-    residual_ds<RY, RX, INT>(R, a.uhi + cb, a.ulo + cb, g, ry0, rx0);
-    __syncthreads();
-  }
-  if (k == 0) {  // ||rho||^2; later norms come from the previous cycle's up kernel
-    float nrm = 0.f;
-#pragma unroll
-    for (int i = 0; i < TY / kBY; ++i)
-#pragma unroll
-      for (int j = 0; j < TX / kBX; ++j) {
-        const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
-        if (INT || (ty0 + ty < g.H && tx0 + tx < g.W)) {
-          const float r = R[(ty + H) * RX + tx + H];
-          nrm = fmaf(r, r, nrm);
-        }
-      }
-    nrm = block_sum(nrm);
-    if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[0], (double)nrm);
-  }
-#pragma unroll
-  for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX, INT>(E, R, g, ry0, rx0, s + 1, s & 1);
-    __syncthreads();
-  }
-  float *e0 = a.e0 + cb;
-#pragma unroll
-  for (int i = 0; i < TY / kBY; ++i)
-#pragma unroll
-    for (int j = 0; j < TX / kBX; ++j) {
-      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
-      const int gy = ty0 + ty, gx = tx0 + tx;
-      if (INT || (gy < g.H && gx < g.W)) e0[(size_t)gy * g.W + gx] = E[(ty + H) * RX + tx + H];
-    }
-  restrict_tile<RY, RX, H, INT>(E, R, g, a.g1, ty0, tx0, a.f1 + (size_t)c * a.g1.plane);
-}
+// ------------------------------------------------------------------ tiles in shared memory
+//
+// A region of RY rows x RXP cells, origin (ry0, rx0) with rx0 even. Cell (y, x)
+// of the region lives in plane x & 1 at plane + y * S + 4 + (x >> 1); each plane
+// row has 4 pad slots on either side (zeroed), so the quad loops may read one
+// cell past the region edge. A plane is padded to 16 mod 32 floats so that the
+// two planes of a cell pair sit in different banks.
 
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg0_down_kernel(L0Args a, Ctrl *ctrl, int k_in) {
-  using S = L0DownShape<NU>;
-  extern __shared__ float sm[];
-  if (*(volatile int *)&ctrl->stopped) return;
-  const int k = cycle_index(ctrl, k_in);
-  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
-  if (region_interior<S::RY, S::RX>(a.g0, ry0, rx0))
-    mg0_down_body<NU, true>(a, ctrl, k, sm, sm + S::RN);
-  else
-    mg0_down_body<NU, false>(a, ctrl, k, sm, sm + S::RN);
-}
-
-template <int NU>
-struct L0UpShape {
-  static constexpr int H = 2 * NU + 1;
-  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
-  static constexpr int CRN = (RY / 2 + 4) * (RX / 2 + 4);
-  static constexpr size_t smem = (2 * RN + CRN) * sizeof(float);
+template <int NU, int TY_ = 32, int TX_ = 128>
+struct Geo {
+  static constexpr int TY = TY_, TX = TX_;
+  static constexpr int HY = 2 * NU + 1;
+  static constexpr int HX = (HY + 3) / 4 * 4;
+  static constexpr int RY = TY + 2 * HY;
+  static constexpr int RXP = TX + 2 * HX;
+  static constexpr int NC = RXP / 2;
+  static constexpr int NQ = NC / 4;
+  static constexpr int S = NC + 8;
+  static constexpr int PLANE = RY * S + ((16 - (RY * S) % 32) + 32) % 32;
+  static constexpr int ARR = 2 * PLANE;
+  static constexpr int CRY = RY / 2 + 4, CRX = RXP / 2 + 4;  // coarse box bound
+  static_assert(RXP % 8 == 0 && S % 4 == 0 && PLANE % 4 == 0, "quad alignment");
 };
 
-// Finest level, second half: e += P e_1, nu2 sweeps on L e = r_k (r_k recomputed
-// from u_k and rho), u_{k+1} = u_k + e in float-float, sum(u_{k+1}) and
-// ||r_{k+1}||^2 with r_{k+1} = r_k - L e (u_{k+1} is the exact float-float sum,
-// so this is its residual up to FP32 rounding of r_k - L e).
-template <int NU, bool INT>
-__device__ __forceinline__ void mg0_up_body(const L0Args &a, Ctrl *ctrl, int k, float *R, float *E,
-                                            float *EC) {
-  using S = L0UpShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX;
-  const LevelGeom &g = a.g0;
+template <class G>
+__device__ __forceinline__ float &at(float *A, int y, int x) {
+  return A[(x & 1) * G::PLANE + y * G::S + 4 + (x >> 1)];
+}
+
+// Loads src (a level array) into the split layout; cells outside the grid read 0.
+// All loads of a thread are issued before its stores, so they overlap.
+template <class G>
+__device__ __forceinline__ void load_split(float *A, const float *__restrict__ src,
+                                           const LevelGeom &g, int ry0, int rx0) {
+  constexpr int NY = (G::RY + kBY - 1) / kBY, NX = (G::RXP + kBX - 1) / kBX;
+  float v[NY][NX];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    const int y = threadIdx.y + kBY * i, gy = ry0 + y;
+    const bool rin = y < G::RY && gy >= 0 && gy < g.H;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int x = threadIdx.x + kBX * j, gx = rx0 + x;
+      v[i][j] = (rin && x < G::RXP && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int y = threadIdx.y + kBY * i, x = threadIdx.x + kBX * j;
+      if (y < G::RY && x < G::RXP) at<G>(A, y, x) = v[i][j];
+    }
+  // pad slots
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int i = tid; i < 2 * G::RY * 8; i += kMgThreads) {
+    const int plane = i / (G::RY * 8), r = i % (G::RY * 8);
+    const int y = r >> 3, j = r & 7;
+    A[plane * G::PLANE + y * G::S + (j < 4 ? j : G::NC + j)] = 0.f;
+  }
+}
+
+template <class G>
+__device__ __forceinline__ void zero_split(float *A) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  float4 *a4 = reinterpret_cast<float4 *>(A);
+  for (int i = tid; i < G::ARR / 4; i += kMgThreads) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Face factors of the region's rows and columns, so that a cell's coefficients
+// are products: e = wy(I) cE(J), w = wy(I) cW(J), s = wx(J) cS(I), n = wx(J) cN(I)
+// (all zero for cells outside the grid). Columns are stored per plane.
+template <class G>
+struct Factors {
+  float wy[G::RY], cS[G::RY], cN[G::RY];
+  float4 wx[2][G::NQ], cE[2][G::NQ], cW[2][G::NQ];
+};
+
+template <class G>
+__device__ __forceinline__ void build_factors(Factors<G> *fa, const LevelGeom &g, int ry0, int rx0) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int y = tid; y < G::RY; y += kMgThreads) {
+    const int gy = ry0 + y;
+    const bool in = gy >= 0 && gy < g.H;
+    fa->wy[y] = in ? wyf(g, gy) : 0.f;
+    fa->cS[y] = (in && gy + 1 < g.H) ? (gy + 1 == g.H - 1 ? g.ey : 1.f) : 0.f;
+    fa->cN[y] = (in && gy > 0) ? (gy == g.H - 1 ? g.ey : 1.f) : 0.f;
+  }
+  float *wx = reinterpret_cast<float *>(fa->wx), *cE = reinterpret_cast<float *>(fa->cE),
+        *cW = reinterpret_cast<float *>(fa->cW);
+  for (int x = tid; x < G::RXP; x += kMgThreads) {
+    const int gx = rx0 + x;
+    const bool in = gx >= 0 && gx < g.W;
+    const int o = (x & 1) * G::NC + (x >> 1);
+    wx[o] = in ? wxf(g, gx) : 0.f;
+    cE[o] = (in && gx + 1 < g.W) ? (gx + 1 == g.W - 1 ? g.ex : 1.f) : 0.f;
+    cW[o] = (in && gx > 0) ? (gx == g.W - 1 ? g.ex : 1.f) : 0.f;
+  }
+}
+
+// One red-black half-sweep (colour col: (gy + gx) & 1 == col) over rows 1..RY-2
+// of the region. A work unit is one quad of same-colour cells of a row: away
+// from the grid border all coefficients are 1; near it they come from the
+// factor tables (cells outside the grid keep their value).
+template <class G>
+__device__ __forceinline__ void half_sweep(float *U, const float *F, const Factors<G> *fa,
+                                           const LevelGeom &g, int ry0, int rx0, int col) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int idx = tid; idx < (G::RY - 2) * G::NQ; idx += kMgThreads) {
+    const int y = 1 + idx / G::NQ;
+    const int q = idx - (y - 1) * G::NQ;
+    const int m0 = q * 4;
+    const int gy = ry0 + y;
+    const bool updE = ((gy + rx0) & 1) == col;  // colour of the even-x cells of this row
+    const int tp = updE ? 0 : G::PLANE, qp = updE ? G::PLANE : 0;
+    float *Trow = U + tp + y * G::S + 4;
+    const float *Qrow = U + qp + y * G::S + 4;
+    const float4 qv = *reinterpret_cast<const float4 *>(Qrow + m0);
+    const float qx = updE ? Qrow[m0 - 1] : Qrow[m0 + 4];
+    const float4 up = *reinterpret_cast<const float4 *>(Trow - G::S + m0);
+    const float4 dn = *reinterpret_cast<const float4 *>(Trow + G::S + m0);
+    const float4 f = *reinterpret_cast<const float4 *>(F + tp + y * G::S + 4 + m0);
+    // west / east neighbours of the four cells
+    const float w0 = updE ? qx : qv.x, w1 = updE ? qv.x : qv.y, w2 = updE ? qv.y : qv.z,
+                w3 = updE ? qv.z : qv.w;
+    const float e0 = updE ? qv.x : qv.y, e1 = updE ? qv.y : qv.z, e2 = updE ? qv.z : qv.w,
+                e3 = updE ? qv.w : qx;
+    const int gx0 = rx0 + 2 * m0;
+    float4 r;
+    if (gy >= 1 && gy <= g.H - 3 && gx0 >= 1 && gx0 + 7 <= g.W - 3) {
+      r.x = 0.25f * ((w0 + e0) + (up.x + dn.x) - f.x);
+      r.y = 0.25f * ((w1 + e1) + (up.y + dn.y) - f.y);
+      r.z = 0.25f * ((w2 + e2) + (up.z + dn.z) - f.z);
+      r.w = 0.25f * ((w3 + e3) + (up.w + dn.w) - f.w);
+    } else {
+      const int pl = updE ? 0 : 1;
+      const float wy = fa->wy[y], cS = fa->cS[y], cN = fa->cN[y];
+      const float4 wx = fa->wx[pl][q], cE = fa->cE[pl][q], cW = fa->cW[pl][q];
+      const float4 old = *reinterpret_cast<const float4 *>(Trow + m0);
+#define GDGS_CELL(C, W_, E_)                                                                  \
+  {                                                                                          \
+    const float ae = wy * cE.C, aw = wy * cW.C, as = wx.C * cS, an = wx.C * cN;              \
+    const float d = (ae + aw) + (as + an);                                                   \
+    r.C = d > 0.f ? (ae * E_ + aw * W_ + as * dn.C + an * up.C - f.C) / d : old.C;           \
+  }
+      GDGS_CELL(x, w0, e0) GDGS_CELL(y, w1, e1) GDGS_CELL(z, w2, e2) GDGS_CELL(w, w3, e3)
+#undef GDGS_CELL
+    }
+    *reinterpret_cast<float4 *>(Trow + m0) = r;
+  }
+}
+
+// Residual f - L u at region cell (y, x) (grid cell (gy, gx) in the grid).
+template <class G>
+__device__ __forceinline__ float tile_residual(float *U, float *F, const LevelGeom &g, int y, int x,
+                                               int gy, int gx) {
+  return residual(g, gy, gx, at<G>(U, y, x), at<G>(U, y, x + 1), at<G>(U, y, x - 1),
+                  at<G>(U, y + 1, x), at<G>(U, y - 1, x), at<G>(F, y, x));
+}
+
+// Sum of the four children's residuals for each coarse cell under the output
+// tile (ty0, tx0) -> fc. Thread (tx, ty) owns coarse columns tx, tx + 32 and
+// rows ty, ty + 8.
+template <class G>
+__device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeom &g,
+                                              const LevelGeom &gc, int ty0, int tx0, float *fc) {
+  const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
+  static_assert(G::TY / 2 % kBY == 0 && G::TX / 2 % kBX == 0, "tile vs threads");
+#pragma unroll
+  for (int i = 0; i < G::TY / 2 / kBY; ++i)
+#pragma unroll
+    for (int j = 0; j < G::TX / 2 / kBX; ++j) {
+      const int CI = (ty0 >> 1) + threadIdx.y + kBY * i;
+      const int CJ = (tx0 >> 1) + threadIdx.x + kBX * j;
+      if (CI >= gc.H || CJ >= gc.W) continue;
+      float sum = 0.f;
+#pragma unroll
+      for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+          const int gy = 2 * CI + di, gx = 2 * CJ + dj;
+          if (gy < g.H && gx < g.W) sum += tile_residual<G>(U, F, g, gy - ry0, gx - rx0, gy, gx);
+        }
+      fc[(size_t)CI * gc.W + CJ] = sum;
+    }
+}
+
+// Coarse values around the region: rows cy0.., columns cx0.. of the coarse level.
+template <class G>
+__device__ __forceinline__ void load_coarse(float *EC, const float *__restrict__ uc,
+                                            const LevelGeom &gc, int cy0, int cx0) {
+  constexpr int NY = (G::CRY + kBY - 1) / kBY, NX = (G::CRX + kBX - 1) / kBX;
+  float v[NY][NX];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    const int y = threadIdx.y + kBY * i, gy = cy0 + y;
+    const bool rin = y < G::CRY && gy >= 0 && gy < gc.H;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int x = threadIdx.x + kBX * j, gx = cx0 + x;
+      v[i][j] = (rin && x < G::CRX && gx >= 0 && gx < gc.W) ? __ldg(uc + (size_t)gy * gc.W + gx) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int y = threadIdx.y + kBY * i, x = threadIdx.x + kBX * j;
+      if (y < G::CRY && x < G::CRX) EC[y * G::CRX + x] = v[i][j];
+    }
+}
+
+// U += P(EC) on the region. Work unit: the 8 cells (4 even-x, 4 odd-x) of a row
+// that share coarse columns m0 .. m0 + 5 of the box; away from the border the
+// weights are the regular 3/4, 1/4 pattern.
+template <class G>
+__device__ __forceinline__ void prolong_tile(float *U, const float *EC, const LevelGeom &g,
+                                             const LevelGeom &gc, int ry0, int rx0, int cy0, int cx0) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int idx = tid; idx < G::RY * G::NQ; idx += kMgThreads) {
+    const int y = idx / G::NQ;
+    const int m0 = (idx - y * G::NQ) * 4;
+    const int gy = ry0 + y;
+    if (gy < 0 || gy >= g.H) continue;
+    const int gx0 = rx0 + 2 * m0;
+    if (gy >= 2 && gy <= g.H - 4 && gx0 >= 2 && gx0 + 7 <= g.W - 4) {
+      const int r0 = (gy >> 1) - cy0;
+      const int r1 = (gy & 1) ? r0 + 1 : r0 - 1;
+      const int c0 = (gx0 >> 1) - 1 - cx0;  // coarse column of cell gx0 minus one
+      float v[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        v[j] = 0.75f * EC[r0 * G::CRX + c0 + j] + 0.25f * EC[r1 * G::CRX + c0 + j];
+      float *Ee = U + y * G::S + 4 + m0;
+      float *Eo = U + G::PLANE + y * G::S + 4 + m0;
+      float4 e = *reinterpret_cast<float4 *>(Ee);
+      float4 o = *reinterpret_cast<float4 *>(Eo);
+      e.x += 0.75f * v[1] + 0.25f * v[0];
+      e.y += 0.75f * v[2] + 0.25f * v[1];
+      e.z += 0.75f * v[3] + 0.25f * v[2];
+      e.w += 0.75f * v[4] + 0.25f * v[3];
+      o.x += 0.75f * v[1] + 0.25f * v[2];
+      o.y += 0.75f * v[2] + 0.25f * v[3];
+      o.z += 0.75f * v[3] + 0.25f * v[4];
+      o.w += 0.75f * v[4] + 0.25f * v[5];
+      *reinterpret_cast<float4 *>(Ee) = e;
+      *reinterpret_cast<float4 *>(Eo) = o;
+    } else {
+      const P1 py = prolong1d(gy, g.shift, g.H0, gc.H);
+      const float *ra = EC + (py.i0 - cy0) * G::CRX;
+      const float *rb = EC + (py.i1 - cy0) * G::CRX;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int x = 2 * m0 + (i & 3) * 2 + (i >> 2);
+        const int gx = rx0 + x;
+        if (gx < 0 || gx >= g.W) continue;
+        const P1 px = prolong1d(gx, g.shift, g.W0, gc.W);
+        const int j0 = px.i0 - cx0, j1 = px.i1 - cx0;
+        const float a0 = ra[j0] + px.w1 * (ra[j1] - ra[j0]);
+        const float a1 = rb[j0] + px.w1 * (rb[j1] - rb[j0]);
+        at<G>(U, y, x) += a0 + py.w1 * (a1 - a0);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ level kernels
+
+struct LvArgs {
+  LevelGeom g, gc;
+  const float *f;    // right-hand side (level >= 1)
+  float *u;          // correction of this level
+  float *fc;         // coarse right-hand side (down)
+  const float *uc;   // coarse correction (up)
+  int level0;        // finest level: right-hand side r_k, u update
+  const float *rho;  // r_0
+  float *rb[2];      // r_{k+1} is written to rb[k & 1]
+  float *uhi, *ulo;  // float-float iterate
+};
+
+__device__ __forceinline__ const float *rhs_of(const LvArgs &a, int k) {
+  if (!a.level0) return a.f;
+  return k == 0 ? a.rho : a.rb[(k - 1) & 1];
+}
+
+// Down: nu1 sweeps on L u = f from u = 0, write u, restrict f - L u.
+template <int NU, int TY_, int TX_>
+__global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k_in, int first) {
+  using G = Geo<NU, TY_, TX_>;
+  extern __shared__ float4 sm4[];
+  float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR;
+  Factors<G> *fa = reinterpret_cast<Factors<G> *>(U + G::ARR);
+  const int k = cycle_index(ctrl, k_in);
+  if (a.level0 ? *(volatile int *)&ctrl->stopped != 0 : should_stop(ctrl, k, first)) return;
+  const LevelGeom &g = a.g;
   const int c = blockIdx.z;
-  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
-  const int ry0 = ty0 - H, rx0 = tx0 - H;
-  const size_t cb = (size_t)c * g.plane;
-  load_region<RY, RX>(R, a.rho + cb, g, ry0, rx0);
-  load_region<RY, RX>(E, a.e0 + cb, g, ry0, rx0);
-  const CoarseBox b = coarse_box(ry0, rx0, RY, RX);
-  load_coarse(EC, a.u1 + (size_t)c * a.g1.plane, a.g1, b);
-  __syncthreads();
-  if (k > 0) residual_ds<RY, RX, INT>(R, a.uhi + cb, a.ulo + cb, g, ry0, rx0);
-  prolong_region<RY, RX>(E, EC, g, a.g1, b, ry0, rx0);
+  const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
+  const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
+  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0);
+  zero_split<G>(U);
+  build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX, INT>(E, R, g, ry0, rx0, s + 1, s & 1);
+    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1);
     __syncthreads();
   }
-  float su = 0.f, rn2 = 0.f;
-  float *uh = a.uhi + cb, *ul = a.ulo + cb;
+  float *uo = a.u + (size_t)c * g.plane;
+  for (int y = threadIdx.y; y < G::TY; y += kBY)
+    for (int x = threadIdx.x; x < G::TX; x += kBX) {
+      const int gy = ty0 + y, gx = tx0 + x;
+      if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = at<G>(U, y + G::HY, x + G::HX);
+    }
+  restrict_tile<G>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
+}
+
+// Up: u += P u_{l+1}, nu2 sweeps, write u. On the finest level instead:
+// u_{k+1} = u_k + e (float-float), r_{k+1} = r_k - L e, ||r_{k+1}||^2, sum(u_{k+1}).
+template <int NU, int TY_, int TX_>
+__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
+  using G = Geo<NU, TY_, TX_>;
+  extern __shared__ float4 sm4[];
+  float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR, *EC = U + G::ARR;
+  Factors<G> *fa = reinterpret_cast<Factors<G> *>(EC + G::CRY * G::CRX + (4 - (G::CRY * G::CRX) % 4) % 4);
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, 0)) return;
+  const LevelGeom &g = a.g;
+  const int c = blockIdx.z;
+  const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
+  const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
+  const int cy0 = (ry0 >> 1) - 1, cx0 = (rx0 >> 1) - 1;
+  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0);
+  load_split<G>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
+  load_coarse<G>(EC, a.uc + (size_t)c * a.gc.plane, a.gc, cy0, cx0);
+  build_factors<G>(fa, g, ry0, rx0);
+  __syncthreads();
+  prolong_tile<G>(U, EC, g, a.gc, ry0, rx0, cy0, cx0);
+  __syncthreads();
 #pragma unroll
-  for (int i = 0; i < TY / kBY; ++i)
-#pragma unroll
-    for (int j = 0; j < TX / kBX; ++j) {
-      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
-      const int gy = ty0 + ty, gx = tx0 + tx;
-      if (INT || (gy < g.H && gx < g.W)) {
-        const size_t p = (size_t)gy * g.W + gx;
-        const int o = (ty + H) * RX + tx + H;
-        float hi = k > 0 ? uh[p] : 0.f, lo = k > 0 ? ul[p] : 0.f;
-        ds_add(hi, lo, E[o]);
-        uh[p] = hi;
-        ul[p] = lo;
-        su += hi + lo;
-        const float rn = INT ? R[o] - ((E[o + 1] + E[o - 1]) + (E[o + RX] + E[o - RX]) - 4.f * E[o])
-                             : residual(g, gy, gx, E[o], E[o + 1], E[o - 1], E[o + RX], E[o - RX], R[o]);
-        rn2 = fmaf(rn, rn, rn2);
+  for (int s = 0; s < 2 * NU; ++s) {
+    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1);
+    __syncthreads();
+  }
+  if (!a.level0) {
+    float *uo = a.u + (size_t)c * g.plane;
+    for (int y = threadIdx.y; y < G::TY; y += kBY)
+      for (int x = threadIdx.x; x < G::TX; x += kBX) {
+        const int gy = ty0 + y, gx = tx0 + x;
+        if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = at<G>(U, y + G::HY, x + G::HX);
       }
+    return;
+  }
+  const size_t cb = (size_t)c * g.plane;
+  float *uh = a.uhi + cb, *ul = a.ulo + cb, *rn = a.rb[k & 1] + cb;
+  constexpr int NY = G::TY / kBY, NX = G::TX / kBX;
+  float vh[NY][NX], vl[NY][NX];
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int gy = ty0 + threadIdx.y + kBY * i, gx = tx0 + threadIdx.x + kBX * j;
+      const bool in = k > 0 && gy < g.H && gx < g.W;
+      const size_t p = (size_t)gy * g.W + gx;
+      vh[i][j] = in ? uh[p] : 0.f;
+      vl[i][j] = in ? ul[p] : 0.f;
+    }
+  float su = 0.f, rn2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const int y = threadIdx.y + kBY * i, x = threadIdx.x + kBX * j;
+      const int gy = ty0 + y, gx = tx0 + x;
+      if (gy >= g.H || gx >= g.W) continue;
+      const size_t p = (size_t)gy * g.W + gx;
+      const int yy = y + G::HY, xx = x + G::HX;
+      float hi = vh[i][j], lo = vl[i][j];
+      ds_add(hi, lo, at<G>(U, yy, xx));
+      uh[p] = hi;
+      ul[p] = lo;
+      su += hi + lo;
+      const float r = tile_residual<G>(U, F, g, yy, xx, gy, gx);
+      rn[p] = r;
+      rn2 = fmaf(r, r, rn2);
     }
   su = block_sum(su);
   if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
@@ -486,131 +567,19 @@ __device__ __forceinline__ void mg0_up_body(const L0Args &a, Ctrl *ctrl, int k, 
   if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
 }
 
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg0_up_kernel(L0Args a, Ctrl *ctrl, int k_in) {
-  using S = L0UpShape<NU>;
-  extern __shared__ float sm[];
-  const int k = cycle_index(ctrl, k_in);
-  if (should_stop(ctrl, k, 0)) return;
-  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
-  if (region_interior<S::RY, S::RX>(a.g0, ry0, rx0))
-    mg0_up_body<NU, true>(a, ctrl, k, sm, sm + S::RN, sm + 2 * S::RN);
-  else
-    mg0_up_body<NU, false>(a, ctrl, k, sm, sm + S::RN, sm + 2 * S::RN);
-}
-
-struct LvArgs {
-  LevelGeom g, gc;
-  float *f, *u;      // this level
-  float *fc;         // coarse right-hand side (down)
-  const float *uc;   // coarse correction (up)
+template <class G>
+struct DownShape {
+  static constexpr size_t smem = 2 * G::ARR * sizeof(float) + sizeof(Factors<G>);
 };
-
-template <int NU>
-struct LvDownShape {
-  static constexpr int H = 2 * NU + 1;
-  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
-  static constexpr size_t smem = 2 * RN * sizeof(float);
+template <class G>
+struct UpShape {
+  static constexpr size_t smem =
+      (2 * G::ARR + (G::CRY * G::CRX + 3) / 4 * 4) * sizeof(float) + sizeof(Factors<G>);
 };
-
-template <int NU, bool INT>
-__device__ __forceinline__ void mg_down_body(const LvArgs &a, float *F, float *U) {
-  using S = LvDownShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX;
-  const LevelGeom &g = a.g;
-  const int c = blockIdx.z;
-  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
-  const int ry0 = ty0 - H, rx0 = tx0 - H;
-  load_region<RY, RX>(F, a.f + (size_t)c * g.plane, g, ry0, rx0);
-  zero_region<RY, RX>(U);
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX, INT>(U, F, g, ry0, rx0, s + 1, s & 1);
-    __syncthreads();
-  }
-  float *uo = a.u + (size_t)c * g.plane;
-#pragma unroll
-  for (int i = 0; i < TY / kBY; ++i)
-#pragma unroll
-    for (int j = 0; j < TX / kBX; ++j) {
-      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
-      const int gy = ty0 + ty, gx = tx0 + tx;
-      if (INT || (gy < g.H && gx < g.W)) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
-    }
-  restrict_tile<RY, RX, H, INT>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
-}
-
-// Level l >= 1, down: nu1 sweeps from u = 0 and residual restriction.
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k_in, int first) {
-  using S = LvDownShape<NU>;
-  extern __shared__ float sm[];
-  const int k = cycle_index(ctrl, k_in);
-  if (should_stop(ctrl, k, first)) return;
-  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
-  if (region_interior<S::RY, S::RX>(a.g, ry0, rx0))
-    mg_down_body<NU, true>(a, sm, sm + S::RN);
-  else
-    mg_down_body<NU, false>(a, sm, sm + S::RN);
-}
-
-template <int NU>
-struct LvUpShape {
-  static constexpr int H = 2 * NU;
-  static constexpr int RY = TY + 2 * H, RX = TX + 2 * H, RN = RY * RX;
-  static constexpr int CRN = (RY / 2 + 4) * (RX / 2 + 4);
-  static constexpr size_t smem = (2 * RN + CRN) * sizeof(float);
-};
-
-template <int NU, bool INT>
-__device__ __forceinline__ void mg_up_body(const LvArgs &a, float *F, float *U, float *EC) {
-  using S = LvUpShape<NU>;
-  constexpr int H = S::H, RY = S::RY, RX = S::RX;
-  const LevelGeom &g = a.g;
-  const int c = blockIdx.z;
-  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
-  const int ry0 = ty0 - H, rx0 = tx0 - H;
-  load_region<RY, RX>(F, a.f + (size_t)c * g.plane, g, ry0, rx0);
-  load_region<RY, RX>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
-  const CoarseBox b = coarse_box(ry0, rx0, RY, RX);
-  load_coarse(EC, a.uc + (size_t)c * a.gc.plane, a.gc, b);
-  __syncthreads();
-  prolong_region<RY, RX>(U, EC, g, a.gc, b, ry0, rx0);
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<RY, RX, INT>(U, F, g, ry0, rx0, s + 1, s & 1);
-    __syncthreads();
-  }
-  float *uo = a.u + (size_t)c * g.plane;
-#pragma unroll
-  for (int i = 0; i < TY / kBY; ++i)
-#pragma unroll
-    for (int j = 0; j < TX / kBX; ++j) {
-      const int ty = threadIdx.y + kBY * i, tx = threadIdx.x + kBX * j;
-      const int gy = ty0 + ty, gx = tx0 + tx;
-      if (INT || (gy < g.H && gx < g.W)) uo[(size_t)gy * g.W + gx] = U[(ty + H) * RX + tx + H];
-    }
-}
-
-// Level l >= 1, up: u += P u_{l+1}, nu2 sweeps.
-template <int NU>
-__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
-  using S = LvUpShape<NU>;
-  extern __shared__ float sm[];
-  const int k = cycle_index(ctrl, k_in);
-  if (should_stop(ctrl, k, 0)) return;
-  const int ry0 = blockIdx.y * TY - S::H, rx0 = blockIdx.x * TX - S::H;
-  if (region_interior<S::RY, S::RX>(a.g, ry0, rx0))
-    mg_up_body<NU, true>(a, sm, sm + S::RN, sm + 2 * S::RN);
-  else
-    mg_up_body<NU, false>(a, sm, sm + S::RN, sm + 2 * S::RN);
-}
 
 // ------------------------------------------------------------------ tail (one CTA per channel)
 //
-// 1024 threads as 32 x 32; levels lt..L live in shared memory as dense arrays.
+// 32 x kTailBY threads; levels lt..L live in shared memory as dense arrays.
 
 struct TailArgs {
   int lt, L;
@@ -627,7 +596,7 @@ __device__ __forceinline__ float tail_nb(const float *U, const LevelGeom &g, int
 }
 
 __device__ __forceinline__ void tail_half_sweep(float *U, const float *F, const LevelGeom &g, int col) {
-  for (int I = threadIdx.y; I < g.H; I += 32) {
+  for (int I = threadIdx.y; I < g.H; I += kTailBY) {
     const int p = (I ^ col) & 1;
     for (int J = p + 2 * threadIdx.x; J < g.W; J += 64) {
       const int o = I * g.W + J;
@@ -665,7 +634,7 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
       tail_half_sweep(U, F, g, s & 1);
       __syncthreads();
     }
-    for (int CI = threadIdx.y; CI < gc.H; CI += 32)
+    for (int CI = threadIdx.y; CI < gc.H; CI += kTailBY)
       for (int CJ = threadIdx.x; CJ < gc.W; CJ += 32) {
         float sum = 0.f;
         for (int di = 0; di < 2; ++di)
@@ -683,9 +652,10 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
     const LevelGeom &g = a.g[a.L];
     float *U = sm + a.off[a.L], *F = U + g.H * g.W;
     const int lane = threadIdx.x, warp = threadIdx.y;
-    for (int i = warp; i < a.nc; i += 32) {
+    for (int i = warp; i < a.nc; i += kTailBY) {
       const double *row = a.Minv + (size_t)i * a.nc;
       double acc = 0.0;
+#pragma unroll 8
       for (int j = lane; j < a.nc; j += 32) acc = fma(__ldg(row + j), -(double)F[j], acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -698,7 +668,7 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
     const LevelGeom &gc = a.g[l + 1];
     float *U = sm + a.off[l], *F = U + g.H * g.W;
     const float *Uc = sm + a.off[l + 1];
-    for (int I = threadIdx.y; I < g.H; I += 32) {
+    for (int I = threadIdx.y; I < g.H; I += kTailBY) {
       const P1 py = prolong1d(I, g.shift, g.H0, gc.H);
       const float *r0 = Uc + py.i0 * gc.W, *r1 = Uc + py.i1 * gc.W;
       for (int J = threadIdx.x; J < g.W; J += 32) {
@@ -792,7 +762,7 @@ __device__ __forceinline__ bool tile_on(const uint8_t *mask, int tiles_x, int i,
 }
 
 // rho(i,j) = [j<W-1] gx(i,j) - [j>=1] gx(i,j-1) + [i<H-1] gy(i,j) - [i>=1] gy(i-1,j),
-// with gradients of tiles whose mask is 0 read as zero.
+// with gradients of tiles whose mask is 0 read as zero; also ||rho||^2.
 __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     ctrl->rtol = a.rtol;
@@ -804,6 +774,7 @@ __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) 
   const float *gxp = a.maps + (size_t)(2 * c) * plane;
   const float *gyp = gxp + plane;
   bool bad = false;
+  float n2 = 0.f;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
        p += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(p / a.W), j = (int)(p - (size_t)i * a.W);
@@ -814,18 +785,22 @@ __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) 
     if (i >= 1 && tile_on(a.mask, a.tiles_x, i - 1, j)) r -= gyp[p - a.W];
     bad |= !isfinite(r);
     a.rho[(size_t)c * plane + p] = r;
+    n2 = fmaf(r, r, n2);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(ctrl, GDGS_ERR_NONFINITE);
+  n2 = block_sum(n2);
+  if (threadIdx.x == 0) atomicAdd(&ctrl->rnorm2[0], (double)n2);
 }
 
 struct FinArgs {
   LevelGeom g0;
-  const float *uhi, *ulo;
+  const float *rho, *uhi, *ulo;
   float *image;
   float mean[GDGS_MAX_CHANNELS];
 };
 
-// image = u + (m_c - mean(u_c)) for the iterate the cycle loop stopped at.
+// image = u + (m_c - mean(u_c)) for the iterate the cycle loop stopped at, and
+// the residual rho - L u of that iterate in float-float arithmetic.
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   const int stopped = ctrl->stopped;
   const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
@@ -834,12 +809,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   const size_t plane = (size_t)g.H * g.W;
   const float shift = (float)((double)a.mean[c] - ctrl->sum_u[kf][c] / (double)plane);
   const size_t cb = (size_t)c * plane;
+  const float *uh = a.uhi + cb, *ul = a.ulo + cb;
+  float r2 = 0.f;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
        p += (size_t)gridDim.x * blockDim.x) {
-    const float hi = kf > 0 ? a.uhi[cb + p] : 0.f;
-    const float lo = kf > 0 ? a.ulo[cb + p] : 0.f;
+    const int i = (int)(p / g.W), j = (int)(p - (size_t)i * g.W);
+    float r = a.rho[cb + p];
+    float hi = 0.f, lo = 0.f;
+    if (kf > 0) {
+      hi = uh[p];
+      lo = ul[p];
+      float sh = 0.f, sl = 0.f;
+      if (j + 1 < g.W) { sh += uh[p + 1] - hi; sl += ul[p + 1] - lo; }
+      if (j > 0) { sh += uh[p - 1] - hi; sl += ul[p - 1] - lo; }
+      if (i + 1 < g.H) { sh += uh[p + g.W] - hi; sl += ul[p + g.W] - lo; }
+      if (i > 0) { sh += uh[p - g.W] - hi; sl += ul[p - g.W] - lo; }
+      r -= sh + sl;
+    }
     a.image[cb + p] = hi + (lo + shift);
+    r2 = fmaf(r, r, r2);
   }
+  r2 = block_sum(r2);
+  if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctrl->mean_set[c] = a.mean[c];
     if (c == 0 && !stopped) ctrl->cycles = kf;
@@ -893,44 +884,46 @@ cudaError_t set_smem(size_t bytes) {
   return e;
 }
 
-template <int NU>
-cudaError_t launch_mg0_down(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
-  const size_t sm = L0DownShape<NU>::smem;
-  cudaError_t e = set_smem<mg0_down_kernel<NU>>(sm);
+template <int NU, int TY_, int TX_>
+cudaError_t launch_mg_down_t(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
+  using G = Geo<NU, TY_, TX_>;
+  const size_t sm = DownShape<G>::smem;
+  cudaError_t e = set_smem<mg_down_kernel<NU, TY_, TX_>>(sm);
   if (e != cudaSuccess) return e;
-  const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg0_down", st); mg0_down_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
+  const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
+  {
+    LaunchScope ls_(a.level0 ? "mg0_down" : "mg_down", st);
+    mg_down_kernel<NU, TY_, TX_><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k, first);
+  }
   return cudaGetLastError();
 }
 
-template <int NU>
-cudaError_t launch_mg0_up(const L0Args &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
-  const size_t sm = L0UpShape<NU>::smem;
-  cudaError_t e = set_smem<mg0_up_kernel<NU>>(sm);
+template <int NU, int TY_, int TX_>
+cudaError_t launch_mg_up_t(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  using G = Geo<NU, TY_, TX_>;
+  const size_t sm = UpShape<G>::smem;
+  cudaError_t e = set_smem<mg_up_kernel<NU, TY_, TX_>>(sm);
   if (e != cudaSuccess) return e;
-  const dim3 grid((a.g0.W + TX - 1) / TX, (a.g0.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg0_up", st); mg0_up_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
+  const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
+  {
+    LaunchScope ls_(a.level0 ? "mg0_up" : "mg_up", st);
+    mg_up_kernel<NU, TY_, TX_><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k);
+  }
   return cudaGetLastError();
 }
+
+inline bool small_level(const LevelGeom &g) { return g.plane < kSmallLevel; }
 
 template <int NU>
 cudaError_t launch_mg_down(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
-  const size_t sm = LvDownShape<NU>::smem;
-  cudaError_t e = set_smem<mg_down_kernel<NU>>(sm);
-  if (e != cudaSuccess) return e;
-  const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg_down", st); mg_down_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k, first); }
-  return cudaGetLastError();
+  return small_level(a.g) ? launch_mg_down_t<NU, 16, 64>(a, ctrl, k, first, C, st)
+                          : launch_mg_down_t<NU, 32, 128>(a, ctrl, k, first, C, st);
 }
 
 template <int NU>
 cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
-  const size_t sm = LvUpShape<NU>::smem;
-  cudaError_t e = set_smem<mg_up_kernel<NU>>(sm);
-  if (e != cudaSuccess) return e;
-  const dim3 grid((a.g.W + TX - 1) / TX, (a.g.H + TY - 1) / TY, C);
-  { LaunchScope ls_("mg_up", st); mg_up_kernel<NU><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k); }
-  return cudaGetLastError();
+  return small_level(a.g) ? launch_mg_up_t<NU, 16, 64>(a, ctrl, k, C, st)
+                          : launch_mg_up_t<NU, 32, 128>(a, ctrl, k, C, st);
 }
 
 template <int NU1, int NU2>
@@ -938,7 +931,7 @@ cudaError_t launch_tail_t(const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int f
                           cudaStream_t st) {
   cudaError_t e = set_smem<mg_tail_kernel<NU1, NU2>>(sm);
   if (e != cudaSuccess) return e;
-  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, dim3(32, 32), sm, st>>>(a, ctrl, k, first); }
+  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, dim3(32, kTailBY), sm, st>>>(a, ctrl, k, first); }
   return cudaGetLastError();
 }
 
@@ -959,13 +952,24 @@ struct Cycle {
   char *ws;
   Ctrl *ctrl;
   int C, nu1, nu2;
-  L0Args l0;
   TailArgs ta;
   size_t tail_smem;
 
   LvArgs level(int l) const {
-    return LvArgs{p->lv[l], p->lv[l + 1], (float *)(ws + p->off_lf[l]), (float *)(ws + p->off_lu[l]),
-                  (float *)(ws + p->off_lf[l + 1]), (const float *)(ws + p->off_lu[l + 1])};
+    LvArgs a{};
+    a.g = p->lv[l];
+    a.gc = p->lv[l + 1];
+    a.f = l > 0 ? (const float *)(ws + p->off_lf[l]) : nullptr;
+    a.u = (float *)(ws + (l > 0 ? p->off_lu[l] : p->off_e0));
+    a.fc = (float *)(ws + p->off_lf[l + 1]);
+    a.uc = (const float *)(ws + p->off_lu[l + 1]);
+    a.level0 = l == 0;
+    a.rho = (const float *)(ws + p->off_rho);
+    a.rb[0] = (float *)(ws + p->off_r[0]);
+    a.rb[1] = (float *)(ws + p->off_r[1]);
+    a.uhi = (float *)(ws + p->off_uhi);
+    a.ulo = (float *)(ws + p->off_ulo);
+    return a;
   }
   unsigned kernels() const { return 2u * (unsigned)p->tail + 2u; }
 
@@ -973,10 +977,10 @@ struct Cycle {
   // before any capture (attributes are set once per kernel and device).
   template <int A, int B>
   cudaError_t prepare_t() const {
-    cudaError_t e = set_smem<mg0_down_kernel<A>>(L0DownShape<A>::smem);
-    if (e == cudaSuccess) e = set_smem<mg_down_kernel<A>>(LvDownShape<A>::smem);
-    if (e == cudaSuccess) e = set_smem<mg0_up_kernel<B>>(L0UpShape<B>::smem);
-    if (e == cudaSuccess) e = set_smem<mg_up_kernel<B>>(LvUpShape<B>::smem);
+    cudaError_t e = set_smem<mg_down_kernel<A, 32, 128>>(DownShape<Geo<A, 32, 128>>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_down_kernel<A, 16, 64>>(DownShape<Geo<A, 16, 64>>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 32, 128>>(UpShape<Geo<B, 32, 128>>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 16, 64>>(UpShape<Geo<B, 16, 64>>::smem);
     if (e == cudaSuccess) e = set_smem<mg_tail_kernel<A, B>>(tail_smem);
     return e;
   }
@@ -992,11 +996,8 @@ struct Cycle {
 
   // k >= 0: explicit cycle index; k < 0: read from ctrl->iter (graph body).
   cudaError_t launch(int k, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) const {
-    cudaError_t e = nu1 == 1 ? launch_mg0_down<1>(l0, ctrl, k, C, st)
-                    : nu1 == 2 ? launch_mg0_down<2>(l0, ctrl, k, C, st)
-                               : launch_mg0_down<3>(l0, ctrl, k, C, st);
-    if (e != cudaSuccess) return e;
-    for (int l = 1; l < p->tail; ++l) {
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < p->tail; ++l) {
       const LvArgs la = level(l);
       const int first = (l == 1);
       e = nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, C, st)
@@ -1006,17 +1007,13 @@ struct Cycle {
     }
     e = launch_tail(nu1, nu2, ta, tail_smem, ctrl, k, p->tail == 1 ? 1 : 0, C, st);
     if (e != cudaSuccess) return e;
-    for (int l = p->tail - 1; l >= 1; --l) {
+    for (int l = p->tail - 1; l >= 0; --l) {
       const LvArgs la = level(l);
       e = nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, C, st)
           : nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, C, st)
                      : launch_mg_up<3>(la, ctrl, k, C, st);
       if (e != cudaSuccess) return e;
     }
-    e = nu2 == 1 ? launch_mg0_up<1>(l0, ctrl, k, C, st)
-        : nu2 == 2 ? launch_mg0_up<2>(l0, ctrl, k, C, st)
-                   : launch_mg0_up<3>(l0, ctrl, k, C, st);
-    if (e != cudaSuccess) return e;
     {
       LaunchScope ls_("mg_advance", st);
       advance_kernel<<<1, 1, 0, st>>>(ctrl, k, h, in_graph, kernels());
@@ -1142,7 +1139,6 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   float *rho = (float *)(ws + p.off_rho);
   float *uhi = (float *)(ws + p.off_uhi);
   float *ulo = (float *)(ws + p.off_ulo);
-  float *e0 = (float *)(ws + p.off_e0);
   cudaError_t e;
 
   DivArgs d{a.maps, a.mask, a.C, a.H, a.W, a.tiles_x, rho, a.rtol, a.max_cycles};
@@ -1177,8 +1173,6 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   cy.C = a.C;
   cy.nu1 = a.nu1;
   cy.nu2 = a.nu2;
-  cy.l0 = L0Args{p.lv[0], p.lv[1], rho, uhi, ulo, e0, (float *)(ws + p.off_lf[1]),
-                 (const float *)(ws + p.off_lu[1])};
   cy.ta.lt = p.tail;
   cy.ta.L = p.levels - 1;
   int off = 0;
@@ -1213,6 +1207,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
 
   FinArgs fa{};
   fa.g0 = p.lv[0];
+  fa.rho = rho;
   fa.uhi = uhi;
   fa.ulo = ulo;
   fa.image = a.image;

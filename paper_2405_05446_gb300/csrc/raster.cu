@@ -28,8 +28,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int C>
 __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   constexpr int Q = 2 * C;
-  __shared__ float s_mx[256], s_my[256], s_ca[256], s_cb[256], s_cc[256], s_opa[256], s_lim[256];
-  __shared__ float s_g[Q][256];
+  constexpr int QV = (Q + 3) / 4;  // float4 slots of the gradient attribute
+  // splat batch, packed so that one pixel-splat evaluation reads 2 broadcast
+  // 16-byte words (plus QV more when the splat contributes)
+  __shared__ float4 s_geo[256];   // mx, my (tile-relative), conic a, conic 2b
+  __shared__ float4 s_geo2[256];  // conic c, opacity, exponent limit, -
+  __shared__ float4 s_g[QV][256];
   const unsigned ntiles = a.use_active ? a.ctrl->n_active : (unsigned)a.T;
   if (blockIdx.x >= ntiles) return;
   const int tile = a.use_active ? (int)a.active[blockIdx.x] : (int)blockIdx.x;
@@ -43,9 +47,9 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   const uint2 rg = a.range[tile];
   const float amin = a.alpha_min, amax = a.alpha_max, tmin = a.t_min;
 
-  float acc[Q];
+  float acc[QV * 4];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) acc[q] = 0.f;
+  for (int q = 0; q < QV * 4; ++q) acc[q] = 0.f;
   float T = 1.f;
   bool done = !inside;
 
@@ -56,29 +60,36 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
       const uint32_t g = a.pval[j];
       const float4 m = a.smean[g];
       const float4 k = a.sconic[g];
-      s_mx[threadIdx.x] = (m.x - x0f) + m.z;
-      s_my[threadIdx.x] = (m.y - y0f) + m.w;
-      s_ca[threadIdx.x] = k.x;
-      s_cb[threadIdx.x] = k.y;
-      s_cc[threadIdx.x] = k.z;
-      s_opa[threadIdx.x] = k.w;
-      s_lim[threadIdx.x] = log2f(k.w / amin) + 1e-3f;
+      s_geo[threadIdx.x] = make_float4((m.x - x0f) + m.z, (m.y - y0f) + m.w, k.x, k.y);
+      s_geo2[threadIdx.x] = make_float4(k.z, k.w, log2f(k.w / amin) + 1e-3f, 0.f);
       const float *gp = a.grad + (size_t)g * Q;
+      float gv[QV * 4];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) s_g[q][threadIdx.x] = gp[q];
+      for (int q = 0; q < QV * 4; ++q) gv[q] = q < Q ? gp[q] : 0.f;
+#pragma unroll
+      for (int v = 0; v < QV; ++v)
+        s_g[v][threadIdx.x] = make_float4(gv[4 * v], gv[4 * v + 1], gv[4 * v + 2], gv[4 * v + 3]);
     }
     __syncthreads();
     const int cnt = min(256u, rg.y - s);
     if (!done) {
       for (int k = 0; k < cnt; ++k) {
-        const float dx = fpx - s_mx[k], dy = fpy - s_my[k];
-        const float p2 = dx * fmaf(s_ca[k], dx, s_cb[k] * dy) + s_cc[k] * dy * dy;
-        if (p2 > s_lim[k]) continue;
-        const float al = fminf(amax, s_opa[k] * ex2_approx(-p2));
+        const float4 ge = s_geo[k];
+        const float4 ge2 = s_geo2[k];
+        const float dx = fpx - ge.x, dy = fpy - ge.y;
+        const float p2 = dx * fmaf(ge.z, dx, ge.w * dy) + ge2.x * dy * dy;
+        if (p2 > ge2.z) continue;
+        const float al = fminf(amax, ge2.y * ex2_approx(-p2));
         if (al < amin) continue;
         const float w = al * T;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) acc[q] = fmaf(s_g[q][k], w, acc[q]);
+        for (int v = 0; v < QV; ++v) {
+          const float4 gg = s_g[v][k];
+          acc[4 * v] = fmaf(gg.x, w, acc[4 * v]);
+          acc[4 * v + 1] = fmaf(gg.y, w, acc[4 * v + 1]);
+          acc[4 * v + 2] = fmaf(gg.z, w, acc[4 * v + 2]);
+          acc[4 * v + 3] = fmaf(gg.w, w, acc[4 * v + 3]);
+        }
         T = T * (1.f - al);
         if (T < tmin) {
           done = true;

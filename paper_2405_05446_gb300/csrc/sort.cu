@@ -52,49 +52,60 @@ radix_hist_kernel(const uint32_t *keys, const unsigned long long *n_dev, unsigne
   if (threadIdx.x <= mask) hist[threadIdx.x * nb + blockIdx.x] = sh[threadIdx.x];
 }
 
-// Exclusive scan of the digit-major histogram (length (mask+1) * nb) in place.
-__global__ void __launch_bounds__(1024)
-radix_scan_kernel(uint32_t *hist, const unsigned long long *n_dev, unsigned cap, unsigned mask) {
-  __shared__ unsigned warp_tot[32];
-  const unsigned n = item_count(n_dev, cap);
-  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
-  const unsigned m = (mask + 1) * nb;
-  const unsigned per = (m + blockDim.x - 1) / blockDim.x;
-  const unsigned b = threadIdx.x * per, e = min(b + per, m);
-  unsigned s = 0;
-  for (unsigned i = b; i < e; ++i) s += hist[i];
-  // block exclusive scan of s
+// Block-wide exclusive scan of 32-bit values for 256 threads; *total = sum.
+__device__ __forceinline__ unsigned scan256(unsigned v, unsigned *total) {
+  __shared__ unsigned wt[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned x = s;
+  unsigned x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) warp_tot[w] = x;
+  if (lane == 31) wt[w] = x;
   __syncthreads();
-  if (w == 0) {
-    unsigned t = warp_tot[lane];
+  unsigned before = 0, all = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    warp_tot[lane] = t;
+  for (int k = 0; k < 8; ++k) {
+    if (k < w) before += wt[k];
+    all += wt[k];
   }
   __syncthreads();
-  unsigned run = x - s + (w > 0 ? warp_tot[w - 1] : 0u);
-  for (unsigned i = b; i < e; ++i) {
-    const unsigned v = hist[i];
-    hist[i] = run;
-    run += v;
+  *total = all;
+  return x - v + before;
+}
+
+// Per digit d (one CTA each): exclusive scan of the block counts hist[d nb ..]
+// in place; the digit's total goes to tot[d].
+__global__ void __launch_bounds__(256)
+radix_scan_digit_kernel(uint32_t *hist, uint32_t *tot, const unsigned long long *n_dev, unsigned cap) {
+  const unsigned n = item_count(n_dev, cap);
+  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  uint32_t *h = hist + (size_t)blockIdx.x * nb;
+  unsigned run = 0;
+  for (unsigned base = 0; base < nb; base += 256) {
+    const unsigned i = base + threadIdx.x;
+    const unsigned v = i < nb ? h[i] : 0u;
+    unsigned t;
+    const unsigned ex = scan256(v, &t);
+    if (i < nb) h[i] = run + ex;
+    run += t;
   }
+  if (threadIdx.x == 0) tot[blockIdx.x] = run;
+}
+
+// Exclusive scan of the digit totals into the digit bases (in place).
+__global__ void __launch_bounds__(256) radix_scan_top_kernel(uint32_t *tot, unsigned ndig) {
+  const unsigned v = threadIdx.x < ndig ? tot[threadIdx.x] : 0u;
+  unsigned t;
+  const unsigned ex = scan256(v, &t);
+  if (threadIdx.x < ndig) tot[threadIdx.x] = ex;
 }
 
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                      uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
-                     unsigned mask, const uint32_t *hist) {
+                     unsigned mask, const uint32_t *hist, const uint32_t *dbase) {
   constexpr int kWarps = kRadixThreads / 32;
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kWarps][256];
@@ -102,7 +113,7 @@ radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t 
   const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
   if (blockIdx.x >= nb) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x <= mask) run[threadIdx.x] = hist[threadIdx.x * nb + blockIdx.x];
+  if (threadIdx.x <= mask) run[threadIdx.x] = dbase[threadIdx.x] + hist[threadIdx.x * nb + blockIdx.x];
   const unsigned base = blockIdx.x * kRadixBlock;
   for (int r = 0; r < kRadixItems; ++r) {
     const unsigned i = base + r * kRadixThreads + threadIdx.x;
@@ -296,11 +307,13 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const unsigned mask = (1u << bits) - 1u;
     if (blocks == 0) break;
     { LaunchScope ls_("radix_hist", st); radix_hist_kernel<<<blocks, kRadixThreads, 0, st>>>(ki, n_dev, cap, shift, mask, hist); }
-    { LaunchScope ls_("radix_scan", st); radix_scan_kernel<<<1, 1024, 0, st>>>(hist, n_dev, cap, mask); }
+    uint32_t *dtot = hist + (size_t)256 * max_blocks;
+    { LaunchScope ls_("radix_scan", st); radix_scan_digit_kernel<<<mask + 1, 256, 0, st>>>(hist, dtot, n_dev, cap); }
+    { LaunchScope ls_("radix_scan_top", st); radix_scan_top_kernel<<<1, 256, 0, st>>>(dtot, mask + 1); }
     {
       LaunchScope ls_("radix_scatter", st);
       radix_scatter_kernel<<<blocks, kRadixThreads, 0, st>>>(
-          ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist);
+          ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist, dtot);
     }
     first = false;
     uint32_t *t = ki; ki = ko; ko = t;
