@@ -91,7 +91,7 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def mg_levels(H: int, W: int, coarse_max: int = 16, tail_budget: int = 8 * 1024):
+def mg_levels(H: int, W: int, coarse_max: int = 8, tail_budget: int = 8 * 1024):
     """Level sizes of the solver (ceil halving until both sides <= coarse_max, at
     least two levels) and the first level run by the single-CTA tail."""
     lv = [(H, W)]

@@ -100,6 +100,9 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
 
   Carver cv;
   p->off_ctrl = cv.take(sizeof(Ctrl));
+  // the cached coarse factor sits at a fixed offset with room for the largest
+  // coarsest grid, so workspaces laid out for other sizes never overwrite it
+  p->off_coarse = cv.take(kCoarseTagBytes + sizeof(double) * (size_t)kMaxCoarse * kMaxCoarse);
   if (n > 0) {
     p->off_smean = cv.take(16 * (size_t)n);
     p->off_sconic = cv.take(16 * (size_t)n);
@@ -129,7 +132,6 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
     p->off_lu[l] = cv.take(b);
     p->off_lf[l] = cv.take(b);
   }
-  p->off_coarse = cv.take(kCoarseTagBytes + sizeof(double) * (size_t)p->nc * p->nc);
   p->total = cv.cur;
   return true;
 }
@@ -313,7 +315,7 @@ void gdgs_default_solver_opts(gdgs_solver_opts *o) {
   o->nu2 = 2;
   o->max_cycles = 30;
   o->rtol = 1e-6f;
-  o->coarse_max_dim = 16;
+  o->coarse_max_dim = 8;
   o->reserved = 0;
 }
 
@@ -468,6 +470,7 @@ int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream) {
   if (c.max_cycles > 0) {  // a solve ran
     const double r0 = c.rnorm2[0];
     rel = r0 > 0 ? sqrt(c.final_rnorm2 / r0) : 0.0;
+    if (status == GDGS_OK && !(rel == rel)) status = GDGS_ERR_NONFINITE;
     if (status == GDGS_OK && !c.stopped && rel > c.rtol) status = GDGS_ERR_NO_CONVERGE;
   }
   if (stats) {

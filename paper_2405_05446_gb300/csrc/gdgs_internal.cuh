@@ -102,8 +102,10 @@ struct CoarseTag {
   unsigned long long magic;
   int H0, W0, levels, Hc, Wc, nc;
   int version;
-  int pad[5];
+  int pad;
+  unsigned long long hash;  // digest of the cached factor
 };
+constexpr int kMaxCoarse = 16 * 16;  // unknowns of the largest coarsest grid
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error; all enqueue on `st`.

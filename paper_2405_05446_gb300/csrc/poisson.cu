@@ -197,7 +197,7 @@ struct Geo {
   static constexpr int PLANE = RY * S + ((16 - (RY * S) % 32) + 32) % 32;
   static constexpr int ARR = 2 * PLANE;
   static constexpr int CRY = RY / 2 + 4, CRX = RXP / 2 + 4;  // coarse box bound
-  static_assert(RXP % 8 == 0 && S % 4 == 0 && PLANE % 4 == 0, "quad alignment");
+  static_assert(RXP % 8 == 0 && S % 4 == 0 && PLANE % 4 == 0 && CRX % 4 == 0, "quad alignment");
 };
 
 template <class G>
@@ -283,10 +283,15 @@ __device__ __forceinline__ void build_factors(Factors<G> *fa, const LevelGeom &g
 template <class G>
 __device__ __forceinline__ void half_sweep(float *U, const float *F, const Factors<G> *fa,
                                            const LevelGeom &g, int ry0, int rx0, int col) {
+  constexpr int NU_ = (G::RY - 2) * G::NQ;
   const int tid = threadIdx.y * kBX + threadIdx.x;
-  for (int idx = tid; idx < (G::RY - 2) * G::NQ; idx += kMgThreads) {
-    const int y = 1 + idx / G::NQ;
-    const int q = idx - (y - 1) * G::NQ;
+  const int lane = threadIdx.x;
+#pragma unroll 1
+  for (int it = 0; it < (NU_ + kMgThreads - 1) / kMgThreads; ++it) {
+    const int idx = tid + kMgThreads * it;
+    const bool act = idx < NU_;
+    const int y = act ? 1 + idx / G::NQ : 1;
+    const int q = act ? idx - (y - 1) * G::NQ : 0;
     const int m0 = q * 4;
     const int gy = ry0 + y;
     const bool updE = ((gy + rx0) & 1) == col;  // colour of the even-x cells of this row
@@ -294,7 +299,13 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
     float *Trow = U + tp + y * G::S + 4;
     const float *Qrow = U + qp + y * G::S + 4;
     const float4 qv = *reinterpret_cast<const float4 *>(Qrow + m0);
-    const float qx = updE ? Qrow[m0 - 1] : Qrow[m0 + 4];
+    // the one neighbour outside the quad comes from the adjacent lane's quad
+    // (same row) or, at a row or warp edge, from shared memory
+    float left = __shfl_up_sync(0xffffffffu, qv.w, 1);
+    float right = __shfl_down_sync(0xffffffffu, qv.x, 1);
+    if (updE && (lane == 0 || q == 0)) left = Qrow[m0 - 1];
+    if (!updE && (lane == kBX - 1 || q == G::NQ - 1)) right = Qrow[m0 + 4];
+    const float qx = updE ? left : right;
     const float4 up = *reinterpret_cast<const float4 *>(Trow - G::S + m0);
     const float4 dn = *reinterpret_cast<const float4 *>(Trow + G::S + m0);
     const float4 f = *reinterpret_cast<const float4 *>(F + tp + y * G::S + 4 + m0);
@@ -324,7 +335,7 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
       GDGS_CELL(x, w0, e0) GDGS_CELL(y, w1, e1) GDGS_CELL(z, w2, e2) GDGS_CELL(w, w3, e3)
 #undef GDGS_CELL
     }
-    *reinterpret_cast<float4 *>(Trow + m0) = r;
+    if (act) *reinterpret_cast<float4 *>(Trow + m0) = r;
   }
 }
 
@@ -405,10 +416,14 @@ __device__ __forceinline__ void prolong_tile(float *U, const float *EC, const Le
       const int r0 = (gy >> 1) - cy0;
       const int r1 = (gy & 1) ? r0 + 1 : r0 - 1;
       const int c0 = (gx0 >> 1) - 1 - cx0;  // coarse column of cell gx0 minus one
-      float v[6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j)
-        v[j] = 0.75f * EC[r0 * G::CRX + c0 + j] + 0.25f * EC[r1 * G::CRX + c0 + j];
+      // c0 = m0 is a multiple of 4 and CRX too: 16- and 8-byte loads
+      const float4 a4 = *reinterpret_cast<const float4 *>(EC + r0 * G::CRX + c0);
+      const float2 a2 = *reinterpret_cast<const float2 *>(EC + r0 * G::CRX + c0 + 4);
+      const float4 b4 = *reinterpret_cast<const float4 *>(EC + r1 * G::CRX + c0);
+      const float2 b2 = *reinterpret_cast<const float2 *>(EC + r1 * G::CRX + c0 + 4);
+      const float v[6] = {0.75f * a4.x + 0.25f * b4.x, 0.75f * a4.y + 0.25f * b4.y,
+                          0.75f * a4.z + 0.25f * b4.z, 0.75f * a4.w + 0.25f * b4.w,
+                          0.75f * a2.x + 0.25f * b2.x, 0.75f * a2.y + 0.25f * b2.y};
       float *Ee = U + y * G::S + 4 + m0;
       float *Eo = U + G::PLANE + y * G::S + 4 + m0;
       float4 e = *reinterpret_cast<float4 *>(Ee);
@@ -694,12 +709,37 @@ __global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl 
 
 // ------------------------------------------------------------------ setup, divergence, finalize
 
+// Order-independent 64-bit digest of the factor (sum of mixed words), so a
+// cached factor is only trusted if its contents are intact.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+__device__ unsigned long long digest(const double *A, int n2) {
+  __shared__ unsigned long long acc;
+  if (threadIdx.x == 0) acc = 0;
+  __syncthreads();
+  unsigned long long h = 0;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x)
+    h += mix64((unsigned long long)__double_as_longlong(A[i]) ^ (0x9e3779b97f4a7c15ull * (i + 1)));
+  atomicAdd(&acc, h);
+  __syncthreads();
+  return acc;
+}
+
 // Builds and inverts M = -L + 11^T / n of the coarsest grid in FP64 (SPD, so
-// Gauss-Jordan without pivoting is stable), unless the tag already matches.
+// Gauss-Jordan without pivoting is stable), unless the cached one in the
+// workspace matches both the grid (tag) and its own digest.
 __global__ void __launch_bounds__(1024)
 coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
   __shared__ int match;
   __shared__ double fcol[260];
+  const int n = g.H * g.W;
   if (threadIdx.x == 0) {
     const CoarseTag t = *tag;
     match = t.magic == want.magic && t.H0 == want.H0 && t.W0 == want.W0 &&
@@ -707,8 +747,10 @@ coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
             t.version == want.version;
   }
   __syncthreads();
-  if (match) return;
-  const int n = g.H * g.W;
+  if (match) {
+    const unsigned long long d = digest(A, n * n);
+    if (d == tag->hash) return;  // uniform: every thread reads the same values
+  }
   const double inv_n = 1.0 / n;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
@@ -739,9 +781,11 @@ coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
     }
     __syncthreads();
   }
+  const unsigned long long d = digest(A, n * n);
   if (threadIdx.x == 0) {
     CoarseTag t = want;
     t.magic = 0;
+    t.hash = d;
     *tag = t;
     __threadfence();
     tag->magic = want.magic;
@@ -847,7 +891,12 @@ __global__ void advance_kernel(Ctrl *ctrl, int k_in, cudaGraphConditionalHandle 
   const int k = k_in >= 0 ? k_in : ctrl->iter;
   if (!ctrl->stopped) {
     const double thr = ctrl->rtol * ctrl->rtol * ctrl->rnorm2[0];
-    if (ctrl->rnorm2[k + 1] <= thr) {
+    const double rk = ctrl->rnorm2[k + 1];
+    if (!(rk == rk) || !(ctrl->rnorm2[0] == ctrl->rnorm2[0])) {  // NaN: stop and report
+      set_status(ctrl, GDGS_ERR_NONFINITE);
+      ctrl->stopped = 1;
+      ctrl->cycles = k + 1;
+    } else if (rk <= thr) {
       ctrl->stopped = 1;
       ctrl->cycles = k + 1;
     }

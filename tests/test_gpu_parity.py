@@ -333,3 +333,49 @@ def test_graph_cache_distinguishes_workspace_layouts():
     ref, _, _ = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
     assert np.isfinite(img.cpu().numpy()).all()
     assert img_err(img.cpu().numpy().astype(np.float64), ref)[1] <= IMG_TOL
+
+
+@pytest.mark.parametrize("coarse", [2, 16])
+@pytest.mark.parametrize("nu", [(1, 1), (3, 2)])
+def test_poisson_solver_options(coarse, nu):
+    """Other coarsest-grid sizes (down to 2x2, up to 16x16) and sweep counts reach
+    the same solution."""
+    rng = np.random.default_rng(coarse * 10 + nu[0])
+    H, W = 150, 211
+    maps = rng.laplace(0, 0.1, (2, 2, H, W)).astype(np.float32)
+    so = G.solver_opts(coarse_max_dim=coarse, nu1=nu[0], nu2=nu[1])
+    img, st = gpu_poisson(maps, [0.5, 0.5], so)
+    ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), [0.5, 0.5])
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    assert img_err(img, ref)[0] <= IMG_TOL
+
+
+def test_coarse_factor_cache_survives_other_layouts_and_detects_corruption():
+    """The FP64 coarse factor cached in the workspace is reused only when it is
+    intact: solves of other shapes in the same buffer, or bytes overwritten inside
+    the cached factor, lead to a rebuild and the same answer."""
+    rng = np.random.default_rng(8)
+    mA = rng.laplace(0, 0.1, (2, 2, 120, 170)).astype(np.float32)
+    mB = rng.laplace(0, 0.1, (1, 2, 300, 90)).astype(np.float32)
+    soA = G.solver_opts(coarse_max_dim=16)
+    soB = G.solver_opts(coarse_max_dim=2)
+    nb = max(G.workspace_size(0, 2, 170, 120, None, soA), G.workspace_size(0, 1, 90, 300, None, soB))
+    ws = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+
+    def solve(m, so):
+        t = torch.as_tensor(m).cuda()
+        img = torch.empty((m.shape[0],) + m.shape[2:], device="cuda")
+        G.poisson_reconstruct(t, [0.5] * m.shape[0], img, ws, sopts=so)
+        st = G.sync_status(ws)
+        assert st["status"] == 0, st
+        return img.cpu().numpy()
+
+    a1 = solve(mA, soA)
+    solve(mB, soB)
+    a2 = solve(mA, soA)
+    assert np.array_equal(a1, a2)
+    ws[8192:8192 + 4096] = torch.randint(0, 255, (4096,), dtype=torch.uint8, device="cuda")
+    a3 = solve(mA, soA)
+    assert np.array_equal(a1, a3)
+    ref = O.poisson_neumann(O.divergence(mA.astype(np.float64)), [0.5, 0.5])
+    assert img_err(a1.astype(np.float64), ref)[0] <= IMG_TOL
