@@ -91,20 +91,14 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def mg_levels(H: int, W: int, coarse_max: int = 8, tail_budget: int = 8 * 1024):
-    """Level sizes of the solver (ceil halving until both sides <= coarse_max, at
-    least two levels) and the first level run by the single-CTA tail."""
+def mg_levels(H: int, W: int, coarse_max: int = 16):
+    """Level sizes of the solver: ceil halving until both sides <= coarse_max, at
+    least two levels; every level but the coarsest runs in the tiled kernels."""
     lv = [(H, W)]
     while len(lv) < 2 or max(lv[-1]) > coarse_max:
         h, w = lv[-1]
         lv.append(((h + 1) // 2, (w + 1) // 2))
-    tail, used = len(lv) - 1, 2 * 4 * lv[-1][0] * lv[-1][1]
-    for l in range(len(lv) - 2, 0, -1):
-        b = 2 * 4 * lv[l][0] * lv[l][1]
-        if used + b > tail_budget:
-            break
-        used, tail = used + b, l
-    return lv, tail
+    return lv, len(lv) - 1
 
 
 def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,

@@ -119,7 +119,7 @@ typedef struct gdgs_raster_opts {
  *   max_cycles      upper bound on V-cycles, 1..64                   (30)
  *   rtol            stop when ||rho - L u||_2 <= rtol ||rho||_2       (1e-6)
  *   coarse_max_dim  coarsen until both grid sides are <= this; the
- *                   coarsest grid is solved directly in FP64, 2..16  (8) */
+ *                   coarsest grid is solved directly in FP64, 2..16  (16) */
 typedef struct gdgs_solver_opts {
   int32_t nu1;
   int32_t nu2;

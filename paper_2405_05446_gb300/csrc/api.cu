@@ -10,7 +10,6 @@ namespace gdgs {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kTailSmemBudget = 8 * 1024;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -87,16 +86,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
   p->levels = levels;
   for (int l = 0; l < levels; ++l) p->lv[l] = level_geom(H, W, l);
   p->nc = p->lv[levels - 1].H * p->lv[levels - 1].W;
-  // tail: first level >= 1 from which all coarser levels fit in shared memory
-  int tail = levels - 1;
-  size_t bytes = 2 * sizeof(float) * (size_t)p->nc;
-  for (int l = levels - 2; l >= 1; --l) {
-    const size_t b = 2 * sizeof(float) * (size_t)p->lv[l].H * p->lv[l].W;
-    if (bytes + b > kTailSmemBudget) break;
-    bytes += b;
-    tail = l;
-  }
-  p->tail = tail;
+  p->tail = levels - 1;  // every level but the coarsest runs in the tiled kernels
 
   Carver cv;
   p->off_ctrl = cv.take(sizeof(Ctrl));
@@ -315,7 +305,7 @@ void gdgs_default_solver_opts(gdgs_solver_opts *o) {
   o->nu2 = 2;
   o->max_cycles = 30;
   o->rtol = 1e-6f;
-  o->coarse_max_dim = 8;
+  o->coarse_max_dim = 16;
   o->reserved = 0;
 }
 

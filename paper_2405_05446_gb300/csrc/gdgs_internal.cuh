@@ -88,7 +88,7 @@ struct Plan {
   size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1
   size_t off_coarse;                                   // tag + FP64 inverse
   int levels;         // number of levels (finest = 0, coarsest = levels-1)
-  int tail;           // first level solved inside one CTA per channel
+  int tail;           // = levels - 1 (levels below it run in the tiled kernels)
   int nc;             // unknowns on the coarsest level
   LevelGeom lv[kMaxLevels];
   size_t total;

@@ -36,8 +36,9 @@
 // few at the border a scalar path with the exact boundary coefficients. Down
 // kernels fuse the pre-sweeps with residual and restriction, up kernels the
 // prolongation with the post-sweeps (and, on the finest level, the update of u,
-// the new residual and its norm). Levels that fit in shared memory run the rest
-// of the V-cycle inside one CTA per channel.
+// the new residual and its norm). Levels under kSmallLevel cells use 16 x 64
+// tiles. The coarsest grid is one FP64 matrix-vector product with the cached
+// inverse, one warp per row over many CTAs.
 //
 // Convergence is decided on the device, so the cycle loop runs as a CUDA graph
 // with a WHILE node: no launch is spent after convergence.
@@ -56,8 +57,6 @@ namespace {
 
 constexpr int kBX = 32, kBY = 8;     // 256 threads
 constexpr int kMgThreads = kBX * kBY;
-constexpr int kTailBY = 8;           // tail CTA: 32 x 8 threads
-constexpr int kTailThreads = 32 * kTailBY;
 // Output tiles of the level kernels: large levels use 32 x 128 cells, levels
 // with fewer cells per channel than kSmallLevel 16 x 64 (more CTAs, shorter
 // serial work per CTA, which is what bounds the small grids).
@@ -592,119 +591,27 @@ struct UpShape {
       (2 * G::ARR + (G::CRY * G::CRX + 3) / 4 * 4) * sizeof(float) + sizeof(Factors<G>);
 };
 
-// ------------------------------------------------------------------ tail (one CTA per channel)
-//
-// 32 x kTailBY threads; levels lt..L live in shared memory as dense arrays.
+// ------------------------------------------------------------------ coarsest grid
 
-struct TailArgs {
-  int lt, L;
-  LevelGeom g[kMaxLevels];
-  int off[kMaxLevels];   // float offset of level l's (U, F) pair in shared memory
-  const float *f_lt;     // global rhs of level lt
-  float *u_lt;           // global correction of level lt (out)
-  const double *Minv;    // [nc][nc]
-  int nc;
-};
-
-__device__ __forceinline__ float tail_nb(const float *U, const LevelGeom &g, int I, int J) {
-  return (I >= 0 && I < g.H && J >= 0 && J < g.W) ? U[I * g.W + J] : 0.f;
-}
-
-__device__ __forceinline__ void tail_half_sweep(float *U, const float *F, const LevelGeom &g, int col) {
-  for (int I = threadIdx.y; I < g.H; I += kTailBY) {
-    const int p = (I ^ col) & 1;
-    for (int J = p + 2 * threadIdx.x; J < g.W; J += 64) {
-      const int o = I * g.W + J;
-      if (interior(g, I, J))
-        U[o] = 0.25f * ((U[o + 1] + U[o - 1]) + (U[o + g.W] + U[o - g.W]) - F[o]);
-      else
-        U[o] = gs_value(g, I, J, tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
-                        tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[o]);
-    }
-  }
-}
-
-template <int NU1, int NU2>
-__global__ void __launch_bounds__(kTailThreads) mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
-  extern __shared__ float sm[];
+// u_L = Minv (-f_L) in FP64 on the coarsest grid: one warp per row of the cached
+// inverse, rows spread over many CTAs (the dense product is the whole solve).
+__global__ void __launch_bounds__(256)
+coarse_solve_kernel(const double *__restrict__ Minv, int nc, const float *__restrict__ f,
+                    float *u, long long plane, Ctrl *ctrl, int k_in, int first) {
   const int k = cycle_index(ctrl, k_in);
   if (should_stop(ctrl, k, first)) return;
-  const int c = blockIdx.x;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  {
-    const LevelGeom &g = a.g[a.lt];
-    float *F = sm + a.off[a.lt] + g.H * g.W;
-    const float *src = a.f_lt + (size_t)c * g.plane;
-    for (int i = tid; i < g.H * g.W; i += kTailThreads) F[i] = __ldg(src + i);
-  }
-  __syncthreads();
-  for (int l = a.lt; l < a.L; ++l) {
-    const LevelGeom &g = a.g[l];
-    const LevelGeom &gc = a.g[l + 1];
-    float *U = sm + a.off[l], *F = U + g.H * g.W;
-    float *Fc = sm + a.off[l + 1] + gc.H * gc.W;
-    for (int i = tid; i < g.H * g.W; i += kTailThreads) U[i] = 0.f;
-    __syncthreads();
-    for (int s = 0; s < 2 * NU1; ++s) {
-      tail_half_sweep(U, F, g, s & 1);
-      __syncthreads();
-    }
-    for (int CI = threadIdx.y; CI < gc.H; CI += kTailBY)
-      for (int CJ = threadIdx.x; CJ < gc.W; CJ += 32) {
-        float sum = 0.f;
-        for (int di = 0; di < 2; ++di)
-          for (int dj = 0; dj < 2; ++dj) {
-            const int I = 2 * CI + di, J = 2 * CJ + dj;
-            if (I >= g.H || J >= g.W) continue;
-            sum += residual(g, I, J, U[I * g.W + J], tail_nb(U, g, I, J + 1), tail_nb(U, g, I, J - 1),
-                            tail_nb(U, g, I + 1, J), tail_nb(U, g, I - 1, J), F[I * g.W + J]);
-          }
-        Fc[CI * gc.W + CJ] = sum;
-      }
-    __syncthreads();
-  }
-  {  // direct FP64 solve on the coarsest grid: u = Minv (-f), one warp per row
-    const LevelGeom &g = a.g[a.L];
-    float *U = sm + a.off[a.L], *F = U + g.H * g.W;
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    for (int i = warp; i < a.nc; i += kTailBY) {
-      const double *row = a.Minv + (size_t)i * a.nc;
-      double acc = 0.0;
-#pragma unroll 8
-      for (int j = lane; j < a.nc; j += 32) acc = fma(__ldg(row + j), -(double)F[j], acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= nc) return;  // whole warp
+  const int c = blockIdx.y;
+  const float *fc = f + (size_t)c * plane;
+  const double *mr = Minv + (size_t)row * nc;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int j = lane; j < nc; j += 32) acc = fma(__ldg(mr + j), -(double)__ldg(fc + j), acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) U[i] = (float)acc;
-    }
-    __syncthreads();
-  }
-  for (int l = a.L - 1; l >= a.lt; --l) {
-    const LevelGeom &g = a.g[l];
-    const LevelGeom &gc = a.g[l + 1];
-    float *U = sm + a.off[l], *F = U + g.H * g.W;
-    const float *Uc = sm + a.off[l + 1];
-    for (int I = threadIdx.y; I < g.H; I += kTailBY) {
-      const P1 py = prolong1d(I, g.shift, g.H0, gc.H);
-      const float *r0 = Uc + py.i0 * gc.W, *r1 = Uc + py.i1 * gc.W;
-      for (int J = threadIdx.x; J < g.W; J += 32) {
-        const P1 px = prolong1d(J, g.shift, g.W0, gc.W);
-        const float a0 = r0[px.i0] + px.w1 * (r0[px.i1] - r0[px.i0]);
-        const float a1 = r1[px.i0] + px.w1 * (r1[px.i1] - r1[px.i0]);
-        U[I * g.W + J] += a0 + py.w1 * (a1 - a0);
-      }
-    }
-    __syncthreads();
-    for (int s = 0; s < 2 * NU2; ++s) {
-      tail_half_sweep(U, F, g, s & 1);
-      __syncthreads();
-    }
-  }
-  {
-    const LevelGeom &g = a.g[a.lt];
-    const float *U = sm + a.off[a.lt];
-    float *dst = a.u_lt + (size_t)c * g.plane;
-    for (int i = tid; i < g.H * g.W; i += kTailThreads) dst[i] = U[i];
-  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) u[(size_t)c * plane + row] = (float)acc;
 }
 
 // ------------------------------------------------------------------ setup, divergence, finalize
@@ -975,34 +882,13 @@ cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t
                           : launch_mg_up_t<NU, 32, 128>(a, ctrl, k, C, st);
 }
 
-template <int NU1, int NU2>
-cudaError_t launch_tail_t(const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int first, int C,
-                          cudaStream_t st) {
-  cudaError_t e = set_smem<mg_tail_kernel<NU1, NU2>>(sm);
-  if (e != cudaSuccess) return e;
-  { LaunchScope ls_("mg_tail", st); mg_tail_kernel<NU1, NU2><<<C, dim3(32, kTailBY), sm, st>>>(a, ctrl, k, first); }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tail(int nu1, int nu2, const TailArgs &a, size_t sm, Ctrl *ctrl, int k, int first,
-                        int C, cudaStream_t st) {
-#define GDGS_TAIL(A, B) \
-  if (nu1 == A && nu2 == B) return launch_tail_t<A, B>(a, sm, ctrl, k, first, C, st);
-  GDGS_TAIL(1, 1) GDGS_TAIL(1, 2) GDGS_TAIL(1, 3)
-  GDGS_TAIL(2, 1) GDGS_TAIL(2, 2) GDGS_TAIL(2, 3)
-  GDGS_TAIL(3, 1) GDGS_TAIL(3, 2) GDGS_TAIL(3, 3)
-#undef GDGS_TAIL
-  return cudaErrorInvalidValue;
-}
-
 // Everything one V-cycle launches, for workspace `ws` laid out by `p`.
 struct Cycle {
   const Plan *p;
   char *ws;
   Ctrl *ctrl;
   int C, nu1, nu2;
-  TailArgs ta;
-  size_t tail_smem;
+  const double *Minv;
 
   LvArgs level(int l) const {
     LvArgs a{};
@@ -1020,7 +906,8 @@ struct Cycle {
     a.ulo = (float *)(ws + p->off_ulo);
     return a;
   }
-  unsigned kernels() const { return 2u * (unsigned)p->tail + 2u; }
+  int L() const { return p->levels - 1; }
+  unsigned kernels() const { return 2u * (unsigned)L() + 2u; }
 
   // Opt-in to large dynamic shared memory for every kernel of the cycle; done
   // before any capture (attributes are set once per kernel and device).
@@ -1030,7 +917,6 @@ struct Cycle {
     if (e == cudaSuccess) e = set_smem<mg_down_kernel<A, 16, 64>>(DownShape<Geo<A, 16, 64>>::smem);
     if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 32, 128>>(UpShape<Geo<B, 32, 128>>::smem);
     if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 16, 64>>(UpShape<Geo<B, 16, 64>>::smem);
-    if (e == cudaSuccess) e = set_smem<mg_tail_kernel<A, B>>(tail_smem);
     return e;
   }
   cudaError_t prepare() const {
@@ -1046,7 +932,7 @@ struct Cycle {
   // k >= 0: explicit cycle index; k < 0: read from ctrl->iter (graph body).
   cudaError_t launch(int k, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) const {
     cudaError_t e = cudaSuccess;
-    for (int l = 0; l < p->tail; ++l) {
+    for (int l = 0; l < L(); ++l) {
       const LvArgs la = level(l);
       const int first = (l == 1);
       e = nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, C, st)
@@ -1054,9 +940,16 @@ struct Cycle {
                      : launch_mg_down<3>(la, ctrl, k, first, C, st);
       if (e != cudaSuccess) return e;
     }
-    e = launch_tail(nu1, nu2, ta, tail_smem, ctrl, k, p->tail == 1 ? 1 : 0, C, st);
-    if (e != cudaSuccess) return e;
-    for (int l = p->tail - 1; l >= 0; --l) {
+    {
+      const LevelGeom &gc = p->lv[L()];
+      const dim3 grid((p->nc + 7) / 8, C);
+      LaunchScope ls_("mg_coarse", st);
+      coarse_solve_kernel<<<grid, 256, 0, st>>>(Minv, p->nc, (const float *)(ws + p->off_lf[L()]),
+                                                (float *)(ws + p->off_lu[L()]), gc.plane, ctrl, k,
+                                                L() == 1 ? 1 : 0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int l = L() - 1; l >= 0; --l) {
       const LvArgs la = level(l);
       e = nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, C, st)
           : nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, C, st)
@@ -1222,21 +1115,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   cy.C = a.C;
   cy.nu1 = a.nu1;
   cy.nu2 = a.nu2;
-  cy.ta.lt = p.tail;
-  cy.ta.L = p.levels - 1;
-  int off = 0;
-  for (int l = 0; l < p.levels; ++l) {
-    cy.ta.g[l] = p.lv[l];
-    if (l >= p.tail) {
-      cy.ta.off[l] = off;
-      off += 2 * p.lv[l].H * p.lv[l].W;
-    }
-  }
-  cy.tail_smem = (size_t)off * sizeof(float);
-  cy.ta.f_lt = (const float *)(ws + p.off_lf[p.tail]);
-  cy.ta.u_lt = (float *)(ws + p.off_lu[p.tail]);
-  cy.ta.Minv = Minv;
-  cy.ta.nc = p.nc;
+  cy.Minv = Minv;
 
   if ((e = cy.prepare()) != cudaSuccess) return e;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
