@@ -208,6 +208,29 @@ GDGS_API int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, c
  * GDGS_ERR_CUDA if the synchronisation itself failed). */
 GDGS_API int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream);
 
+/* Step 3 without a caller workspace (the paper has no counterpart: this is a
+ * deployment variant). For callers that cannot allocate device memory where they
+ * need the solve - inside a CUDA stream capture, in a plug-in whose host
+ * application owns the device allocator, or in a loop that forbids allocation
+ * after start-up - the scratch lives in a fixed 32 MiB __device__ array of the
+ * library, held on every GPU that loads it until the process exits.
+ *   Arguments as for gdgs_poisson_reconstruct; `stats` (host, nullable): when
+ *   given, the call waits for `stream` and fills it (and returns the device
+ *   status), otherwise it only enqueues.
+ *   Sizes whose workspace (gdgs_workspace_size(0, ...)) exceeds 32 MiB are
+ *   rejected with GDGS_ERR_WORKSPACE before anything is enqueued; about
+ *   640 x 480 x 3 or 1024 x 1024 x 1 fit.
+ *   No cudaMalloc, cudaFree or other allocating call is made. The first call on
+ *   a device looks the array's address up (cudaGetSymbolAddress) and should come
+ *   before any stream capture on that device.
+ *   All calls share the one array, which keeps the last call's contents (what
+ *   must start at zero is cleared by each call); calls that overlap on the GPU
+ *   race and must be ordered by the caller (one stream, or synchronisation). */
+GDGS_API int gdgs_poisson_reconstruct_static(const float *grad_maps, const uint8_t *tile_mask,
+                                             int32_t channels, int32_t height, int32_t width,
+                                             const float *mean, const gdgs_solver_opts *sopts,
+                                             float *image, gdgs_solve_stats *stats, void *stream);
+
 /* ---- diagnostics (host side; not needed on the render path) ---------------- */
 
 /* Per-kernel timing record filled by gdgs_profile_end(). */
