@@ -30,6 +30,8 @@ WORKLOADS = {
                   "normal; 1920x1080, 3 channels, multigrid V(2,2) to rel. residual 1e-6, mean 0.5",
     "tiny64": "1000 gradient Gaussians, 64x64, 3 channels, rtol 1e-6, mean 0.5",
     "prims4k": "1M gradient Gaussians on 50 primitives, 3840x2160, 3 channels, rtol 1e-6",
+    "lap1080p": "the prims1080p Gaussians carrying one Laplacian value per channel (Eq. gdgs, "
+                "Laplace(0,0.05)) instead of a gradient: composite = rho, no divergence",
 }
 METRIC = "1080p views/s (splat+Poisson, FP32 path, rel. residual <= 1e-6)"
 HBM_FALLBACK_GBS = 6800.0

@@ -65,17 +65,25 @@ enum {
   GDGS_ERR_CAPACITY = 7      /* more (tile, splat) pairs than the pair buffer holds (device) */
 };
 
+/* What each Gaussian carries (gdgs_gaussians.attribute). */
+enum {
+  GDGS_ATTR_GRADIENT = 0,  /* (gx, gy) per channel; the image is recovered from div g */
+  GDGS_ATTR_LAPLACIAN = 1  /* one value per channel: the Laplacian field itself
+                              (Eq. gdgs, the paper-literal form) */
+};
+
 /* Gaussians, structure of arrays, all device pointers (Sec. 1.2, Eq. 3dgs):
  *   mean    [n][3]  centre tau_k in world space
  *   scale   [n][3]  linear per-axis scale, S = diag(scale)
  *   quat    [n][4]  rotation (w, x, y, z); normalised by the library
  *   opacity [n]     alpha_k
- *   grad    [n][channels][2]  gradient attribute (gx, gy) per channel
+ *   grad    [n][channels][K]  attribute per channel: K = 2 (gx, gy) for
+ *                   GDGS_ATTR_GRADIENT, K = 1 (A_k of Eq. gdgs) for GDGS_ATTR_LAPLACIAN
  * Every array must be 4-byte aligned; n >= 0, 1 <= channels <= 4. */
 typedef struct gdgs_gaussians {
   int64_t n;
   int32_t channels;
-  int32_t reserved;
+  int32_t attribute;  /* GDGS_ATTR_GRADIENT (0) or GDGS_ATTR_LAPLACIAN (1) */
   const float *mean;
   const float *scale;
   const float *quat;
@@ -119,14 +127,17 @@ typedef struct gdgs_raster_opts {
  *   max_cycles      upper bound on V-cycles, 1..64                   (30)
  *   rtol            stop when ||rho - L u||_2 <= rtol ||rho||_2       (1e-6)
  *   coarse_max_dim  coarsen until both grid sides are <= this; the
- *                   coarsest grid is solved directly in FP64, 2..16  (16) */
+ *                   coarsest grid is solved directly in FP64, 2..16  (16)
+ *   rho_threshold   t of the hard threshold T(x) = x if |x| >= t else 0
+ *                   applied to the Laplacian field rho before the solve
+ *                   (Eq. thresh); 0 keeps rho as it is                 (0) */
 typedef struct gdgs_solver_opts {
   int32_t nu1;
   int32_t nu2;
   int32_t max_cycles;
   float rtol;
   int32_t coarse_max_dim;
-  int32_t reserved;
+  float rho_threshold;
 } gdgs_solver_opts;
 
 /* Filled by gdgs_sync_status() from the workspace after the stream has drained. */
@@ -173,8 +184,10 @@ GDGS_API int gdgs_project(const gdgs_gaussians *g, const gdgs_camera *cam,
                  void *ws, size_t ws_bytes, void *stream);
 
 /* Steps 1-2 (Eq. gdgs2d): project, bin the splats into 16x16 tiles, sort each
- * tile's splats front to back, and composite the gradient attribute into
- *   grad_maps  device [channels][2][height][width] (component 0 = gx, 1 = gy).
+ * tile's splats front to back, and composite the attribute into
+ *   grad_maps  device [channels][K][height][width]: K = 2 (component 0 = gx,
+ *              1 = gy) for gradient Gaussians, K = 1 (the field rho) for
+ *              Laplacian Gaussians.
  * tile_mask  device [ceil(height/16)][ceil(width/16)] bytes, or NULL.
  *   With a mask, only tiles some splat reaches are written and the mask says
  *   which (1) — other tiles of grad_maps are left untouched and mean zero.
@@ -196,9 +209,20 @@ GDGS_API int gdgs_poisson_reconstruct(const float *grad_maps, const uint8_t *til
                              const float *mean, const gdgs_solver_opts *sopts,
                              float *image, void *ws, size_t ws_bytes, void *stream);
 
+/* Step 3 for a Laplacian field given directly (Eq. p2d with rho = the composite
+ * of Laplacian Gaussians, Eq. gdgs / Eq. gdgs2d): T(rho) per the solver options,
+ * then the Neumann solve as in gdgs_poisson_reconstruct.
+ * rho  device [channels][height][width]; tile_mask as written by
+ *      gdgs_render_gradients (tiles with mask 0 are read as zero), or NULL. */
+GDGS_API int gdgs_poisson_reconstruct_rho(const float *rho, const uint8_t *tile_mask,
+                                          int32_t channels, int32_t height, int32_t width,
+                                          const float *mean, const gdgs_solver_opts *sopts,
+                                          float *image, void *ws, size_t ws_bytes, void *stream);
+
 /* Steps 1-3 of Algorithm 1's render path in one call: project, rasterise the
- * sparse gradient maps (kept inside the workspace), divergence and Poisson solve
- * into image (device [channels][height][width], 16-byte aligned). */
+ * sparse attribute maps (kept inside the workspace), the divergence (gradient
+ * Gaussians) or the field itself (Laplacian Gaussians), and the Poisson solve into
+ * image (device [channels][height][width], 16-byte aligned). */
 GDGS_API int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const float *mean,
                      const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts,
                      float *image, void *ws, size_t ws_bytes, void *stream);

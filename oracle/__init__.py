@@ -17,7 +17,9 @@ What it computes, step by step, all in float64:
                     Neumann 5-point Laplacian; the constant left free by the
                     Neumann problem (Sec. 2.1, "with possible constant difference")
                     is fixed by a supplied per-channel mean
-  render_view       the three render steps of Algorithm 1 in order
+  threshold         the hard threshold T of Eq. thresh
+  render_view       the three render steps of Algorithm 1 in order, for gradient
+                    Gaussians (divergence first) or Laplacian Gaussians (Eq. gdgs)
 
 Parity against values printed in the paper is unpinned for the whole pipeline:
 the paper prints no worked example. Each function is pinned instead by closed
@@ -124,22 +126,25 @@ def depth_order(proj: np.ndarray) -> np.ndarray:
 def render_gradients(scene, cam, opts: RasterOpts = RasterOpts(), mode: str = "box",
                      pixels=None, nthreads: int = 0, amb_rel: float = 2e-5,
                      depth_rel: float = 0.0, proj=None):
-    """Composite the per-Gaussian gradient attributes front to back (Eq. gdgs2d).
+    """Composite the per-Gaussian attributes front to back (Eq. gdgs2d, Eq. color).
 
     At pixel centre p: for each Gaussian k in depth order, G = exp(-exp_coef d^T conic d)
     with d = p - mean2d, a = min(alpha_max, alpha_k G); a < alpha_min is skipped;
-    acc += g_k * a * T; T *= (1 - a); stop once T < t_min.
+    acc += c_k * a * T; T *= (1 - a); stop once T < t_min.
 
-    mode "all_pairs" visits every Gaussian at every pixel (the plain definition);
-    mode "box" skips Gaussians whose footprint box misses the pixel (same result).
-    Returns (maps, ambiguous): maps [C][2][H][W] (or [P][C][2] for a pixel list),
-    ambiguous a uint8 flag per pixel (see oracle_raster.c).
+    The attribute c_k is scene.grad: [N][C][2] gradients (gx, gy) or [N][C] Laplacian
+    values (Eq. gdgs). mode "all_pairs" visits every Gaussian at every pixel (the plain
+    definition); mode "box" skips Gaussians whose footprint box misses the pixel (same
+    result). Returns (maps, ambiguous): maps [C][2][H][W] or [C][H][W] (or [P][C][2] /
+    [P][C] for a pixel list), ambiguous a uint8 flag per pixel (see oracle_raster.c).
     """
     lib = _load()
     if proj is None:
         proj = project(scene, cam, opts)
     grad = _f32(scene.grad)
     C = grad.shape[1]
+    K = grad.shape[2] if grad.ndim == 3 else 1
+    Q = C * K
     order = depth_order(proj)
     W, H = cam.width, cam.height
     optv = np.array([opts.exp_coef, opts.alpha_min, opts.alpha_max, opts.t_min, amb_rel,
@@ -148,19 +153,28 @@ def render_gradients(scene, cam, opts: RasterOpts = RasterOpts(), mode: str = "b
     if mode not in ("box", "all_pairs"):
         raise ValueError(mode)
     if pixels is None:
-        out = np.zeros((H * W, 2 * C), dtype=np.float64)
+        out = np.zeros((H * W, Q), dtype=np.float64)
         amb = np.zeros(H * W, dtype=np.uint8)
-        lib.oracle_composite(_ptr(proj), _ptr(grad), C, _ptr(order), order.shape[0], W, H,
+        lib.oracle_composite(_ptr(proj), _ptr(grad), Q, _ptr(order), order.shape[0], W, H,
                              use_box, _ptr(optv), None, 0, nthreads, _ptr(out), _ptr(amb))
-        maps = out.reshape(H, W, C, 2).transpose(2, 3, 0, 1).copy()
+        if K == 2:
+            maps = out.reshape(H, W, C, 2).transpose(2, 3, 0, 1).copy()
+        else:
+            maps = out.reshape(H, W, C).transpose(2, 0, 1).copy()
         return maps, amb.reshape(H, W)
     pix = np.ascontiguousarray(pixels, dtype=np.int64)
-    out = np.zeros((pix.shape[0], 2 * C), dtype=np.float64)
+    out = np.zeros((pix.shape[0], Q), dtype=np.float64)
     amb = np.zeros(pix.shape[0], dtype=np.uint8)
-    lib.oracle_composite(_ptr(proj), _ptr(grad), C, _ptr(order), order.shape[0], W, H,
+    lib.oracle_composite(_ptr(proj), _ptr(grad), Q, _ptr(order), order.shape[0], W, H,
                          use_box, _ptr(optv), _ptr(pix), pix.shape[0], nthreads, _ptr(out),
                          _ptr(amb))
-    return out.reshape(-1, C, 2), amb
+    return (out.reshape(-1, C, 2) if K == 2 else out.reshape(-1, C)), amb
+
+
+def threshold(rho: np.ndarray, t: float) -> np.ndarray:
+    """T(x) = x if |x| >= t else 0, elementwise (Eq. thresh)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.where(np.abs(rho) >= t, rho, 0.0)
 
 
 def divergence(maps: np.ndarray) -> np.ndarray:
@@ -238,10 +252,16 @@ def poisson_neumann(rho: np.ndarray, mean) -> np.ndarray:
     return out
 
 
-def render_view(scene, cam, mean, opts: RasterOpts = RasterOpts(), nthreads: int = 0):
-    """Algorithm 1's render steps: project + composite (Eq. gdgs2d), divergence,
-    Neumann Poisson solve (Eq. p2d) with the constant fixed by `mean`.
-    Returns (image [C][H][W], maps [C][2][H][W], ambiguous [H][W])."""
+def render_view(scene, cam, mean, opts: RasterOpts = RasterOpts(), nthreads: int = 0,
+                rho_threshold: float = 0.0):
+    """Algorithm 1's render steps: project + composite (Eq. gdgs2d), the Laplacian field
+    (the divergence of gradient maps, or the composite itself for Laplacian Gaussians,
+    Eq. gdgs), the hard threshold T when rho_threshold > 0 (Eq. thresh), and the Neumann
+    Poisson solve (Eq. p2d) with the constant fixed by `mean`.
+    Returns (image [C][H][W], maps, ambiguous [H][W])."""
     maps, amb = render_gradients(scene, cam, opts, mode="box", nthreads=nthreads)
-    img = poisson_neumann(divergence(maps), mean)
+    rho = divergence(maps) if maps.ndim == 4 else maps
+    if rho_threshold > 0:
+        rho = threshold(rho, rho_threshold)
+    img = poisson_neumann(rho, mean)
     return img, maps, amb

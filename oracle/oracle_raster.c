@@ -145,11 +145,11 @@ typedef struct {
  * a relative margin of its threshold. */
 static int composite_pixel(double px, double py, const int64_t *cand, int64_t m,
                            int check_box, const double *proj, const float *grad,
-                           int C, const orc_opts *o, double *acc) {
+                           int Q, const orc_opts *o, double *acc) {
   double T = 1.0;
   int amb = 0;
   double last_depth = -1.0;
-  for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0;
+  for (int q = 0; q < Q; ++q) acc[q] = 0.0;
   for (int64_t i = 0; i < m; ++i) {
     int64_t g = cand[i];
     const double *r = proj + g * ORC_STRIDE;
@@ -170,7 +170,7 @@ static int composite_pixel(double px, double py, const int64_t *cand, int64_t m,
       amb = 1;
     last_depth = r[ORC_KEY];
     double wgt = a * T;
-    for (int q = 0; q < 2 * C; ++q) acc[q] += (double)grad[g * 2 * C + q] * wgt;
+    for (int q = 0; q < Q; ++q) acc[q] += (double)grad[g * Q + q] * wgt;
     T *= (1.0 - a);
     if (fabs(T - o->tmin) <= o->amb_rel * o->tmin) amb = 1;
     if (T < o->tmin) break;
@@ -180,11 +180,13 @@ static int composite_pixel(double px, double py, const int64_t *cand, int64_t m,
 
 /* opt: exp_coef, alpha_min, alpha_max, t_min, amb_rel, depth_rel.
  * order: the valid Gaussians sorted by (depth, index).
- * Full image (pixels == NULL): out is [H*W][2C] in raster order, amb [H*W].
- * Pixel list: out is [n_pixels][2C], amb [n_pixels]; pixel id = row*W + col.
+ * Q: attribute floats per Gaussian (2 per channel for gradients, 1 per channel
+ * for the Laplacian field of Eq. gdgs).
+ * Full image (pixels == NULL): out is [H*W][Q] in raster order, amb [H*W].
+ * Pixel list: out is [n_pixels][Q], amb [n_pixels]; pixel id = row*W + col.
  * use_box = 0 composites every candidate at every pixel (the plain definition);
  * use_box = 1 pre-filters by the footprint box (same result, faster). */
-void oracle_composite(const double *proj, const float *grad, int C,
+void oracle_composite(const double *proj, const float *grad, int Q,
                       const int64_t *order, int64_t n_order, int W, int H,
                       int use_box, const double *opt, const int64_t *pixels,
                       int64_t n_pixels, int nthreads, double *out,
@@ -200,8 +202,8 @@ void oracle_composite(const double *proj, const float *grad, int C,
     for (int64_t p = 0; p < n_pixels; ++p) {
       int64_t row = pixels[p] / W, col = pixels[p] % W;
       amb[p] = (uint8_t)composite_pixel(col + 0.5, row + 0.5, order, n_order,
-                                        use_box, proj, grad, C, &o,
-                                        out + p * 2 * C);
+                                        use_box, proj, grad, Q, &o,
+                                        out + p * Q);
     }
     return;
   }
@@ -224,7 +226,7 @@ void oracle_composite(const double *proj, const float *grad, int C,
       for (int col = 0; col < W; ++col) {
         int64_t p = (int64_t)row * W + col;
         amb[p] = (uint8_t)composite_pixel(col + 0.5, py, rowc, m, use_box, proj,
-                                          grad, C, &o, out + p * 2 * C);
+                                          grad, Q, &o, out + p * Q);
       }
     }
     free(rowc);

@@ -11,7 +11,8 @@ import dataclasses
 from . import _abi
 
 __all__ = ["GDGSError", "raster_opts", "solver_opts", "workspace_size", "project",
-           "render_gradients", "poisson_reconstruct", "render_view", "sync_status",
+           "render_gradients", "poisson_reconstruct", "poisson_reconstruct_rho", "render_view",
+           "sync_status",
            "status_string", "Renderer", "gaussians_to_device", "kernel_launch_count",
            "profile_begin", "profile_end"]
 
@@ -63,7 +64,9 @@ def _ptr(t):
 
 @dataclasses.dataclass
 class DeviceGaussians:
-    """Gaussian attribute tensors resident on the device (layouts of gdgs_gaussians)."""
+    """Gaussian attribute tensors resident on the device (layouts of gdgs_gaussians).
+
+    grad is [n][C][2] (gradient Gaussians) or [n][C] (Laplacian Gaussians)."""
     mean: "object"
     scale: "object"
     quat: "object"
@@ -78,12 +81,17 @@ class DeviceGaussians:
     def channels(self) -> int:
         return int(self.grad.shape[1])
 
+    @property
+    def attribute(self) -> int:
+        return _abi.ATTR_LAPLACIAN if self.grad.dim() == 2 else _abi.ATTR_GRADIENT
+
     def struct(self) -> _abi.Gaussians:
         for t in (self.mean, self.scale, self.quat, self.opacity, self.grad):
             if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
                 raise ValueError("Gaussian tensors must be contiguous float32 CUDA tensors")
-        return _abi.Gaussians(self.n, self.channels, 0, _ptr(self.mean), _ptr(self.scale),
-                              _ptr(self.quat), _ptr(self.opacity), _ptr(self.grad))
+        return _abi.Gaussians(self.n, self.channels, self.attribute, _ptr(self.mean),
+                              _ptr(self.scale), _ptr(self.quat), _ptr(self.opacity),
+                              _ptr(self.grad))
 
 
 def gaussians_to_device(scene, device="cuda") -> DeviceGaussians:
@@ -139,6 +147,15 @@ def poisson_reconstruct(maps, mean, image, ws, mask=None, sopts=None, stream=Non
     _check(_lib().gdgs_poisson_reconstruct(_ptr(maps), _ptr(mask), int(C), int(H), int(W),
                                            _mean_array(mean, C), sopts, _ptr(image), _ptr(ws),
                                            ws.numel(), _stream(stream)), "gdgs_poisson_reconstruct")
+
+
+def poisson_reconstruct_rho(rho, mean, image, ws, mask=None, sopts=None, stream=None) -> None:
+    """Solve L u = T(rho) for a Laplacian field given directly ([C][H][W])."""
+    C, H, W = rho.shape
+    _check(_lib().gdgs_poisson_reconstruct_rho(_ptr(rho), _ptr(mask), int(C), int(H), int(W),
+                                               _mean_array(mean, C), sopts, _ptr(image), _ptr(ws),
+                                               ws.numel(), _stream(stream)),
+           "gdgs_poisson_reconstruct_rho")
 
 
 def render_view(g: DeviceGaussians, cam, mean, image, ws, ropts=None, sopts=None, stream=None) -> None:
@@ -204,7 +221,8 @@ class Renderer:
         import torch
         C, H, W = self.shape
         if maps is None:
-            maps = torch.empty((C, 2, H, W), dtype=torch.float32, device=self.device)
+            shape = (C, H, W) if g.attribute == _abi.ATTR_LAPLACIAN else (C, 2, H, W)
+            maps = torch.empty(shape, dtype=torch.float32, device=self.device)
         render_gradients(g, cam, maps, self.ws, mask, self.ropts, stream)
         return maps
 

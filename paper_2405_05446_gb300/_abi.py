@@ -30,8 +30,12 @@ _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
 
 
+ATTR_GRADIENT = 0
+ATTR_LAPLACIAN = 1
+
+
 class Gaussians(ctypes.Structure):
-    _fields_ = [("n", _i64), ("channels", _i32), ("reserved", _i32), ("mean", _p),
+    _fields_ = [("n", _i64), ("channels", _i32), ("attribute", _i32), ("mean", _p),
                 ("scale", _p), ("quat", _p), ("opacity", _p), ("grad", _p)]
 
 
@@ -47,7 +51,7 @@ class RasterOpts(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", _i32), ("nu2", _i32), ("max_cycles", _i32), ("rtol", _f),
-                ("coarse_max_dim", _i32), ("reserved", _i32)]
+                ("coarse_max_dim", _i32), ("rho_threshold", _f)]
 
 
 class SolveStats(ctypes.Structure):
@@ -81,6 +85,9 @@ PROTOTYPES = {
     "gdgs_poisson_reconstruct": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(_f),
                                                 ctypes.POINTER(SolverOpts), _p, _p, ctypes.c_size_t,
                                                 _p]),
+    "gdgs_poisson_reconstruct_rho": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(_f),
+                                                    ctypes.POINTER(SolverOpts), _p, _p,
+                                                    ctypes.c_size_t, _p]),
     "gdgs_render_view": (ctypes.c_int, [ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
                                         ctypes.POINTER(_f), ctypes.POINTER(RasterOpts),
                                         ctypes.POINTER(SolverOpts), _p, _p, ctypes.c_size_t, _p]),

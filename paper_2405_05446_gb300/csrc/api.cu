@@ -49,7 +49,8 @@ bool raster_opts_ok(const gdgs_raster_opts &o) {
 bool solver_opts_ok(const gdgs_solver_opts &o) {
   return o.nu1 >= 1 && o.nu1 <= 3 && o.nu2 >= 1 && o.nu2 <= 3 && o.max_cycles >= 1 &&
          o.max_cycles <= kMaxCycles && isfinite(o.rtol) && o.rtol >= 0.f &&
-         o.coarse_max_dim >= 2 && o.coarse_max_dim <= 16;
+         o.coarse_max_dim >= 2 && o.coarse_max_dim <= 16 && isfinite(o.rho_threshold) &&
+         o.rho_threshold >= 0.f;
 }
 
 }  // namespace
@@ -148,8 +149,14 @@ gdgs_solver_opts sopts_or_default(const gdgs_solver_opts *o) {
   return r;
 }
 
+int attr_floats(const gdgs_gaussians *g) {
+  return g->attribute == GDGS_ATTR_LAPLACIAN ? g->channels : 2 * g->channels;
+}
+
 int check_gaussians(const gdgs_gaussians *g) {
   if (!g || g->n < 0 || g->channels < 1 || g->channels > GDGS_MAX_CHANNELS) return GDGS_ERR_INVALID_ARG;
+  if (g->attribute != GDGS_ATTR_GRADIENT && g->attribute != GDGS_ATTR_LAPLACIAN)
+    return GDGS_ERR_INVALID_ARG;
   if (g->n > 0) {
     const void *ptrs[5] = {g->mean, g->scale, g->quat, g->opacity, g->grad};
     for (const void *q : ptrs)
@@ -183,6 +190,7 @@ ProjectArgs project_args(const gdgs_gaussians *g, const gdgs_camera *cam,
   a.grad = g->grad;
   a.n = g->n;
   a.C = g->channels;
+  a.Q = attr_floats(g);
   memcpy(a.w2c, cam->world_to_cam, sizeof(a.w2c));
   a.fx = cam->fx;
   a.fy = cam->fy;
@@ -270,7 +278,7 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
   r.active = active;
   r.use_active = (use_mask && g->n > 0) ? 1 : 0;
   if (use_mask && g->n == 0) return cudaSuccess;  // nothing active, mask already zero
-  r.C = g->channels;
+  r.Q = attr_floats(g);
   r.alpha_min = ro.alpha_min;
   r.alpha_max = ro.alpha_max;
   r.t_min = ro.t_min;
@@ -306,7 +314,7 @@ void gdgs_default_solver_opts(gdgs_solver_opts *o) {
   o->max_cycles = 30;
   o->rtol = 1e-6f;
   o->coarse_max_dim = 16;
-  o->reserved = 0;
+  o->rho_threshold = 0.f;
 }
 
 const char *gdgs_status_string(int s) {
@@ -371,11 +379,11 @@ int gdgs_render_gradients(const gdgs_gaussians *g, const gdgs_camera *cam,
   return to_status(raster_path(g, cam, ro, p, w, grad_maps, tile_mask, tile_mask != nullptr, st));
 }
 
-int gdgs_poisson_reconstruct(const float *grad_maps, const uint8_t *tile_mask, int32_t channels,
-                             int32_t height, int32_t width, const float *mean,
-                             const gdgs_solver_opts *sopts, float *image, void *ws,
-                             size_t ws_bytes, void *stream) {
-  if (!grad_maps || !image || !mean || !aligned(grad_maps, 16) || !aligned(image, 16))
+static int poisson_common(const float *field, int input_is_rho, const uint8_t *tile_mask,
+                          int32_t channels, int32_t height, int32_t width, const float *mean,
+                          const gdgs_solver_opts *sopts, float *image, void *ws, size_t ws_bytes,
+                          void *stream) {
+  if (!field || !image || !mean || !aligned(field, 16) || !aligned(image, 16))
     return GDGS_ERR_INVALID_ARG;
   if (channels < 1 || channels > GDGS_MAX_CHANNELS) return GDGS_ERR_INVALID_ARG;
   const gdgs_raster_opts ro = ropts_or_default(nullptr);
@@ -385,15 +393,18 @@ int gdgs_poisson_reconstruct(const float *grad_maps, const uint8_t *tile_mask, i
   for (int c = 0; c < channels; ++c)
     if (!isfinite(mean[c])) return GDGS_ERR_INVALID_ARG;
   const size_t plane = (size_t)width * height * channels;
-  const char *ib = (const char *)image, *gb = (const char *)grad_maps;
-  if (ib < gb + plane * 2 * sizeof(float) && gb < ib + plane * sizeof(float)) return GDGS_ERR_INVALID_ARG;
+  const size_t fbytes = plane * (input_is_rho ? 1 : 2) * sizeof(float);
+  const char *ib = (const char *)image, *gb = (const char *)field;
+  if (ib < gb + fbytes && gb < ib + plane * sizeof(float)) return GDGS_ERR_INVALID_ARG;
   int s;
   if ((s = check_ws(ws, ws_bytes, p))) return s;
   cudaStream_t st = (cudaStream_t)stream;
   char *w = (char *)ws;
   if (cudaMemsetAsync(w + p.off_ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return GDGS_ERR_CUDA;
   PoissonArgs a{};
-  a.maps = grad_maps;
+  a.maps = field;
+  a.input_is_rho = input_is_rho;
+  a.threshold = so.rho_threshold;
   a.mask = tile_mask;
   a.C = channels;
   a.H = height;
@@ -409,6 +420,22 @@ int gdgs_poisson_reconstruct(const float *grad_maps, const uint8_t *tile_mask, i
   a.ws = w;
   a.ctrl = (Ctrl *)(w + p.off_ctrl);
   return to_status(run_poisson(a, st));
+}
+
+int gdgs_poisson_reconstruct(const float *grad_maps, const uint8_t *tile_mask, int32_t channels,
+                             int32_t height, int32_t width, const float *mean,
+                             const gdgs_solver_opts *sopts, float *image, void *ws,
+                             size_t ws_bytes, void *stream) {
+  return poisson_common(grad_maps, 0, tile_mask, channels, height, width, mean, sopts, image, ws,
+                        ws_bytes, stream);
+}
+
+int gdgs_poisson_reconstruct_rho(const float *rho, const uint8_t *tile_mask, int32_t channels,
+                                 int32_t height, int32_t width, const float *mean,
+                                 const gdgs_solver_opts *sopts, float *image, void *ws,
+                                 size_t ws_bytes, void *stream) {
+  return poisson_common(rho, 1, tile_mask, channels, height, width, mean, sopts, image, ws,
+                        ws_bytes, stream);
 }
 
 int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const float *mean,
@@ -433,6 +460,8 @@ int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const floa
   if (e != cudaSuccess) return GDGS_ERR_CUDA;
   PoissonArgs a{};
   a.maps = maps;
+  a.input_is_rho = g->attribute == GDGS_ATTR_LAPLACIAN;
+  a.threshold = so.rho_threshold;
   a.mask = mask;
   a.C = g->channels;
   a.H = cam->height;

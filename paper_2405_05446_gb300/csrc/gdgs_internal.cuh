@@ -36,8 +36,11 @@ struct Ctrl {
   double rtol;
   double rnorm2[kMaxCycles + 1];             // ||rho - L u_k||^2, k = 0..
   double sum_u[kMaxCycles + 1][GDGS_MAX_CHANNELS];  // sum of u_k per channel
-  double final_rnorm2;                       // residual of u when not stopped
+  double final_rnorm2;                       // residual of the returned iterate
   double mean_set[GDGS_MAX_CHANNELS];
+  double rho_sum[GDGS_MAX_CHANNELS];         // sum and sum of squares of rho per channel
+  double rho_sq[GDGS_MAX_CHANNELS];
+  float rho_mean[GDGS_MAX_CHANNELS];         // the constant removed from rho (least squares)
 };
 
 // Diagnostics hooks around every kernel launch (diag.cu).
@@ -113,6 +116,7 @@ struct ProjectArgs {
   const float *mean, *scale, *quat, *opacity, *grad;
   int64_t n;
   int C;
+  int Q;           // attribute floats per Gaussian
   float w2c[12];
   float fx, fy, cx, cy, znear;
   int W, H, tiles_x, tiles_y;
@@ -162,15 +166,17 @@ struct RasterArgs {
   const uint2 *range;       // [T]
   const uint32_t *active;   // [T] active tile ids (when use_active)
   int use_active;           // 1: only active tiles (count in ctrl->n_active)
-  int C, W, H, tiles_x, T;
+  int Q, W, H, tiles_x, T;  // Q attribute floats per Gaussian = output planes
   float alpha_min, alpha_max, t_min;
-  float *maps;              // [C][2][H][W]
+  float *maps;              // [Q][H][W]
   Ctrl *ctrl;
 };
 cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st);
 
 struct PoissonArgs {
-  const float *maps;        // [C][2][H][W]
+  const float *maps;        // [C][2][H][W], or [C][H][W] when input_is_rho
+  int input_is_rho;         // the field rho itself instead of gradient maps
+  float threshold;          // hard threshold on rho (0: none)
   const uint8_t *mask;      // [tiles_y][tiles_x] or null
   int C, H, W, tiles_x;
   float mean[GDGS_MAX_CHANNELS];

@@ -208,7 +208,7 @@ __device__ __forceinline__ float &at(float *A, int y, int x) {
 // All loads of a thread are issued before its stores, so they overlap.
 template <class G>
 __device__ __forceinline__ void load_split(float *A, const float *__restrict__ src,
-                                           const LevelGeom &g, int ry0, int rx0) {
+                                           const LevelGeom &g, int ry0, int rx0, float off = 0.f) {
   constexpr int NY = (G::RY + kBY - 1) / kBY, NX = (G::RXP + kBX - 1) / kBX;
   float v[NY][NX];
 #pragma unroll
@@ -218,7 +218,7 @@ __device__ __forceinline__ void load_split(float *A, const float *__restrict__ s
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       const int x = threadIdx.x + kBX * j, gx = rx0 + x;
-      v[i][j] = (rin && x < G::RXP && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) : 0.f;
+      v[i][j] = (rin && x < G::RXP && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) - off : 0.f;
     }
   }
 #pragma unroll
@@ -475,6 +475,12 @@ __device__ __forceinline__ const float *rhs_of(const LvArgs &a, int k) {
   return k == 0 ? a.rho : a.rb[(k - 1) & 1];
 }
 
+// r_0 = rho - mean(rho): a field whose sum is not zero (possible for the
+// composite of Laplacian values) is solved in the least-squares sense.
+__device__ __forceinline__ float rhs_offset(const LvArgs &a, const Ctrl *ctrl, int k, int c) {
+  return (a.level0 && k == 0) ? ctrl->rho_mean[c] : 0.f;
+}
+
 // Down: nu1 sweeps on L u = f from u = 0, write u, restrict f - L u.
 template <int NU, int TY_, int TX_>
 __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k_in, int first) {
@@ -488,7 +494,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
-  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0);
+  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
   zero_split<G>(U);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
   const int cy0 = (ry0 >> 1) - 1, cx0 = (rx0 >> 1) - 1;
-  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0);
+  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
   load_split<G>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
   load_coarse<G>(EC, a.uc + (size_t)c * a.gc.plane, a.gc, cy0, cx0);
   build_factors<G>(fa, g, ry0, rx0);
@@ -643,10 +649,20 @@ __device__ unsigned long long digest(const double *A, int n2) {
 // Gauss-Jordan without pivoting is stable), unless the cached one in the
 // workspace matches both the grid (tag) and its own digest.
 __global__ void __launch_bounds__(1024)
-coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
+coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl *ctrl, int C,
+                    long long npx) {
   __shared__ int match;
   __shared__ double fcol[260];
   const int n = g.H * g.W;
+  if (threadIdx.x == 0) {  // ||rho - mean(rho)||^2 and the means, from the divergence sums
+    double r2 = 0.0;
+    for (int c = 0; c < C; ++c) {
+      const double m = ctrl->rho_sum[c] / (double)npx;
+      ctrl->rho_mean[c] = (float)m;
+      r2 += fmax(ctrl->rho_sq[c] - ctrl->rho_sum[c] * m, 0.0);
+    }
+    ctrl->rnorm2[0] = r2;
+  }
   if (threadIdx.x == 0) {
     const CoarseTag t = *tag;
     match = t.magic == want.magic && t.H0 == want.H0 && t.W0 == want.W0 &&
@@ -702,6 +718,8 @@ coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want) {
 struct DivArgs {
   const float *maps;
   const uint8_t *mask;
+  int input_is_rho;
+  float threshold;
   int C, H, W, tiles_x;
   float *rho;
   float rtol;
@@ -713,7 +731,8 @@ __device__ __forceinline__ bool tile_on(const uint8_t *mask, int tiles_x, int i,
 }
 
 // rho(i,j) = [j<W-1] gx(i,j) - [j>=1] gx(i,j-1) + [i<H-1] gy(i,j) - [i>=1] gy(i-1,j),
-// with gradients of tiles whose mask is 0 read as zero; also ||rho||^2.
+// with gradients of tiles whose mask is 0 read as zero (or rho read directly for
+// Laplacian fields); then the hard threshold T of Eq. thresh when t > 0; ||rho||^2.
 __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     ctrl->rtol = a.rtol;
@@ -722,25 +741,35 @@ __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) 
   }
   const int c = blockIdx.y;
   const size_t plane = (size_t)a.H * a.W;
-  const float *gxp = a.maps + (size_t)(2 * c) * plane;
+  const float *gxp = a.maps + (size_t)(a.input_is_rho ? c : 2 * c) * plane;
   const float *gyp = gxp + plane;
   bool bad = false;
-  float n2 = 0.f;
+  float n2 = 0.f, s1 = 0.f;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
        p += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(p / a.W), j = (int)(p - (size_t)i * a.W);
     float r = 0.f;
-    if (j + 1 < a.W && tile_on(a.mask, a.tiles_x, i, j)) r += gxp[p];
-    if (j >= 1 && tile_on(a.mask, a.tiles_x, i, j - 1)) r -= gxp[p - 1];
-    if (i + 1 < a.H && tile_on(a.mask, a.tiles_x, i, j)) r += gyp[p];
-    if (i >= 1 && tile_on(a.mask, a.tiles_x, i - 1, j)) r -= gyp[p - a.W];
+    if (a.input_is_rho) {
+      if (tile_on(a.mask, a.tiles_x, i, j)) r = gxp[p];
+    } else {
+      if (j + 1 < a.W && tile_on(a.mask, a.tiles_x, i, j)) r += gxp[p];
+      if (j >= 1 && tile_on(a.mask, a.tiles_x, i, j - 1)) r -= gxp[p - 1];
+      if (i + 1 < a.H && tile_on(a.mask, a.tiles_x, i, j)) r += gyp[p];
+      if (i >= 1 && tile_on(a.mask, a.tiles_x, i - 1, j)) r -= gyp[p - a.W];
+    }
     bad |= !isfinite(r);
+    if (a.threshold > 0.f && !(fabsf(r) >= a.threshold)) r = 0.f;
     a.rho[(size_t)c * plane + p] = r;
     n2 = fmaf(r, r, n2);
+    s1 += r;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(ctrl, GDGS_ERR_NONFINITE);
   n2 = block_sum(n2);
-  if (threadIdx.x == 0) atomicAdd(&ctrl->rnorm2[0], (double)n2);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctrl->rho_sq[c], (double)n2);
+    atomicAdd(&ctrl->rho_sum[c], (double)s1);
+  }
 }
 
 struct FinArgs {
@@ -765,7 +794,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < plane;
        p += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(p / g.W), j = (int)(p - (size_t)i * g.W);
-    float r = a.rho[cb + p];
+    float r = a.rho[cb + p] - ctrl->rho_mean[c];
     float hi = 0.f, lo = 0.f;
     if (kf > 0) {
       hi = uh[p];
@@ -1083,7 +1112,8 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   float *ulo = (float *)(ws + p.off_ulo);
   cudaError_t e;
 
-  DivArgs d{a.maps, a.mask, a.C, a.H, a.W, a.tiles_x, rho, a.rtol, a.max_cycles};
+  DivArgs d{a.maps, a.mask, a.input_is_rho, a.threshold, a.C, a.H, a.W, a.tiles_x, rho, a.rtol,
+            a.max_cycles};
   {
     const size_t plane = (size_t)a.H * a.W;
     int bx = (int)((plane + 255) / 256);
@@ -1105,7 +1135,11 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   want.version = 1;
   CoarseTag *tag = (CoarseTag *)(ws + p.off_coarse);
   double *Minv = (double *)(ws + p.off_coarse + kCoarseTagBytes);
-  { LaunchScope ls_("coarse_setup", st); coarse_setup_kernel<<<1, 1024, 0, st>>>(gcoarse, Minv, tag, want); }
+  {
+    LaunchScope ls_("coarse_setup", st);
+    coarse_setup_kernel<<<1, 1024, 0, st>>>(gcoarse, Minv, tag, want, ctrl, a.C,
+                                            (long long)a.H * a.W);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   Cycle cy{};

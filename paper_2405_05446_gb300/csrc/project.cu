@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
     bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) &&
                   isfinite(s1) && isfinite(s2) && isfinite(qw) && isfinite(qx) &&
                   isfinite(qy) && isfinite(qz) && isfinite(opa);
-    for (int q = 0; q < 2 * a.C; ++q) finite = finite && isfinite(a.grad[i * 2 * a.C + q]);
+    for (int q = 0; q < a.Q; ++q) finite = finite && isfinite(a.grad[i * a.Q + q]);
     if (!finite) set_status(a.ctrl, GDGS_ERR_NONFINITE);
 
     float key = __fmaf_rn(a.w2c[8], mx, __fmaf_rn(a.w2c[9], my, __fmaf_rn(a.w2c[10], mz, a.w2c[11])));

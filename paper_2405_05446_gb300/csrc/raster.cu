@@ -1,4 +1,5 @@
-// Tile rasteriser of the gradient attribute (K5).
+// Tile rasteriser of the per-Gaussian attribute (K5): the gradient (gx, gy per
+// channel) or, in the paper-literal form, the Laplacian value per channel.
 //
 // One CTA of 256 threads per non-empty 16x16 tile, one pixel per thread. The
 // tile's splats are already in front-to-back order (sort.cu); they are staged in
@@ -25,9 +26,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-template <int C>
+template <int Q>
 __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
-  constexpr int Q = 2 * C;
   constexpr int QV = (Q + 3) / 4;  // float4 slots of the gradient attribute
   // splat batch, packed so that one pixel-splat evaluation reads 2 broadcast
   // 16-byte words (plus QV more when the splat contributes)
@@ -111,11 +111,13 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
 cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st) {
   if (a.T == 0) return cudaSuccess;
   LaunchScope ls_("raster", st);
-  switch (a.C) {
+  switch (a.Q) {
     case 1: raster_kernel<1><<<a.T, 256, 0, st>>>(a); break;
     case 2: raster_kernel<2><<<a.T, 256, 0, st>>>(a); break;
     case 3: raster_kernel<3><<<a.T, 256, 0, st>>>(a); break;
     case 4: raster_kernel<4><<<a.T, 256, 0, st>>>(a); break;
+    case 6: raster_kernel<6><<<a.T, 256, 0, st>>>(a); break;
+    case 8: raster_kernel<8><<<a.T, 256, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

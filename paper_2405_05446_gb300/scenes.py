@@ -236,6 +236,15 @@ def image_from_gradients_test_image(h: int, w: int, seed: int = 0) -> np.ndarray
     return smooth + 0.05 * rng.standard_normal((h, w))
 
 
+def with_laplacian_attribute(scene: Scene, seed: int = 0, value_scale: float = 0.05) -> Scene:
+    """The same Gaussians carrying one Laplacian value per channel (the A_k of Eq. gdgs,
+    drawn i.i.d. Laplace(0, value_scale)) instead of a gradient."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    vals = rng.laplace(0.0, value_scale, (scene.n, scene.channels))
+    return Scene(scene.mean, scene.scale, scene.quat, scene.opacity,
+                 np.ascontiguousarray(vals, dtype=np.float32))
+
+
 # Named workloads -----------------------------------------------------------------
 
 def workload(name: str):
@@ -244,6 +253,9 @@ def workload(name: str):
         return tiny_scene(0), tiny_camera(), np.full(3, 0.5), 1e-6
     if name == "prims1080p":
         return primitives_scene(0), metric_camera(), np.full(3, 0.5), 1e-6
+    if name == "lap1080p":
+        sc, cam, mean, rtol = workload("prims1080p")
+        return with_laplacian_attribute(sc), cam, mean, rtol
     if name == "prims4k":
         cam = metric_camera(3840, 2160)
         return (primitives_scene(0, n=1_000_000, n_prims=50, orient_camera=cam), cam,

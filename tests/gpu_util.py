@@ -38,7 +38,8 @@ def gpu_maps(scene, cam, ropts=None, with_mask=False):
     C = scene.channels
     nbytes = G.workspace_size(scene.n, C, cam.width, cam.height, ropts, None)
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    maps = torch.full((C, 2, cam.height, cam.width), float("nan"), device="cuda")
+    shape = (C, cam.height, cam.width) if scene.grad.ndim == 2 else (C, 2, cam.height, cam.width)
+    maps = torch.full(shape, float("nan"), device="cuda")
     mask = None
     if with_mask:
         mask = torch.zeros(((cam.height + 15) // 16, (cam.width + 15) // 16), dtype=torch.uint8, device="cuda")

@@ -379,3 +379,60 @@ def test_coarse_factor_cache_survives_other_layouts_and_detects_corruption():
     assert np.array_equal(a1, a3)
     ref = O.poisson_neumann(O.divergence(mA.astype(np.float64)), [0.5, 0.5])
     assert img_err(a1.astype(np.float64), ref)[0] <= IMG_TOL
+
+
+# ------------------------------------------------------------------ Laplacian Gaussians (Eq. gdgs)
+
+def test_laplacian_field_matches_oracle():
+    scene = S.with_laplacian_attribute(S.tiny_scene(2))
+    cam = S.tiny_camera(96, 64)
+    gm, _, st = gpu_maps(scene, cam)
+    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    assert st["status"] == 0 and gm.shape == om.shape == (3, 64, 96)
+    ok = amb == 0
+    assert np.abs(gm - om)[:, ok].max() <= MAP_TOL * np.abs(om).max()
+
+
+def _well_posed_threshold(scene, rho, amb, candidates):
+    """A threshold t for which no pixel's decision |rho| >= t lies within the composite
+    error bound the map parity test enforces (MAP_TOL * max|rho| for clear pixels, plus
+    alpha_min * max|A| where a Gaussian sits at the alpha_min cut). The decision is
+    discrete: at such a t both sides must take the same one at every pixel."""
+    a = np.abs(rho)
+    ref = a.max()
+    margin = np.where(amb[None] > 0, np.abs(scene.grad).max() / 255.0 + MAP_TOL * ref, MAP_TOL * ref)
+    for t in candidates:
+        t = float(np.float32(t))
+        if np.all(np.abs(a - t) > margin):
+            return t
+    return None
+
+
+@pytest.mark.parametrize("t", [0.0, 0.004])
+def test_render_view_laplacian_with_threshold(t):
+    # a small ragged view: few enough pixels that thresholds with a decision margin exist
+    scene, cam = _small_prims(n=3000, w=136, h=100)
+    scene = S.with_laplacian_attribute(scene)
+    mean = [0.5, 0.4, 0.6]
+    if t > 0:
+        rho, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+        t = _well_posed_threshold(scene, rho, amb, [t * (1 + 0.005 * i) for i in range(400)])
+        assert t is not None
+        assert 0.2 < (np.abs(rho) < t).mean() < 0.9  # the threshold removes a real share
+    img, st = _render(scene, cam, mean, sopts=G.solver_opts(rho_threshold=t))
+    ref, _, _ = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()), rho_threshold=t)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+def test_poisson_reconstruct_rho_entry_point():
+    rng = np.random.default_rng(12)
+    rho = rng.laplace(0, 0.05, (2, 70, 90)).astype(np.float32)
+    ws = torch.empty(G.workspace_size(0, 2, 90, 70), dtype=torch.uint8, device="cuda")
+    img = torch.empty((2, 70, 90), device="cuda")
+    G.poisson_reconstruct_rho(torch.as_tensor(rho).cuda(), [0.5, 0.5], img, ws,
+                              sopts=G.solver_opts(rho_threshold=0.03))
+    st = G.sync_status(ws)
+    ref = O.poisson_neumann(O.threshold(rho.astype(np.float64), np.float32(0.03)), [0.5, 0.5])
+    assert st["status"] == 0
+    assert img_err(img.cpu().numpy().astype(np.float64), ref)[0] <= IMG_TOL

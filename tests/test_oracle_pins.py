@@ -435,3 +435,29 @@ def test_tiny_pipeline_golden_samples():
         assert maps[c, 1, i, j] == pytest.approx(s["gy"], abs=1e-12)
         assert img[c, i, j] == pytest.approx(s["img"], abs=1e-10)
     assert int(amb.sum()) == ref["ambiguous"]
+
+
+def test_laplacian_attribute_hand_fixture_and_threshold():
+    """Scalar (Laplacian) attributes composite by the same rule (Eq. gdgs2d with the
+    c_k of Eq. gdgs); T keeps values at or above t in magnitude (Eq. thresh)."""
+    fx = json.load(open(os.path.join(GOLDEN, "composite_hand.json")))
+    cam = S.tiny_camera(8, 8)
+    rows = _hand_rows(fx["alpha"], fx["depth"], [(3.5, 2.5)] * 3)
+    sc = _hand_scene(fx["g"])
+    sc = S.Scene(sc.mean, sc.scale, sc.quat, sc.opacity, np.ascontiguousarray(sc.grad[:, :, 0]))
+    out, _ = O.render_gradients(sc, cam, mode="all_pairs", pixels=[19], proj=rows)
+    assert out.shape == (1, 1) and out[0, 0] == pytest.approx(fx["expected"], abs=1e-15)
+    x = np.array([-0.5, -0.003, -0.002, 0.0, 0.002, 0.003, 0.7])
+    np.testing.assert_array_equal(O.threshold(x, 0.003), [-0.5, -0.003, 0, 0, 0, 0.003, 0.7])
+
+
+def test_laplacian_scene_box_equals_all_pairs():
+    sc = S.with_laplacian_attribute(S.tiny_scene(4, n=40))
+    cam = S.tiny_camera(32, 32)
+    a, _ = O.render_gradients(sc, cam, mode="all_pairs")
+    b, _ = O.render_gradients(sc, cam, mode="box")
+    assert a.shape == (3, 32, 32) and np.array_equal(a, b)
+    img, maps, _ = O.render_view(sc, cam, [0.5, 0.5, 0.5])
+    r = maps - O.laplacian_neumann(img)
+    np.testing.assert_allclose(r, np.broadcast_to(maps.mean(axis=(1, 2), keepdims=True), r.shape),
+                               atol=1e-10)
