@@ -27,7 +27,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "prims1080p": "200k gradient Gaussians on the surfaces of 20 boxes/spheres (90%) + 10% "
                   "uniform, log-scales N(-5,0.7), gradients Laplace(0,0.1) along the projected "
-                  "normal; 1920x1080, 3 channels, multigrid V(2,2) to rel. residual 1e-6, mean 0.5",
+                  "normal; 1920x1080, 3 channels, multigrid V(2,1) with red-black SOR (omega 1.2) to "
+                  "rel. residual 1e-6, mean 0.5",
     "tiny64": "1000 gradient Gaussians, 64x64, 3 channels, rtol 1e-6, mean 0.5",
     "prims4k": "1M gradient Gaussians on 50 primitives, 3840x2160, 3 channels, rtol 1e-6",
     "lap1080p": "the prims1080p Gaussians carrying one Laplacian value per channel (Eq. gdgs, "
@@ -93,28 +94,38 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def mg_levels(H: int, W: int, coarse_max: int = 16):
-    """Level sizes of the solver: ceil halving until both sides <= coarse_max, at
-    least two levels; every level but the coarsest runs in the tiled kernels."""
+TAIL_CELLS = 12288  # levels with at most this many cells per channel run in the tail kernel
+
+
+def mg_levels(H: int, W: int, coarse_max: int = 8):
+    """Level sizes of the solver (ceil halving until both sides <= coarse_max, at
+    least two levels) and the first level of the tail kernel: levels 0 .. t-1
+    run in the tiled kernels, t .. coarsest in one CTA per channel."""
     lv = [(H, W)]
     while len(lv) < 2 or max(lv[-1]) > coarse_max:
         h, w = lv[-1]
         lv.append(((h + 1) // 2, (w + 1) // 2))
-    return lv, len(lv) - 1
+    t = 1
+    while t < len(lv) - 1 and lv[t][0] * lv[t][1] > TAIL_CELLS:
+        t += 1
+    return lv, t
 
 
 def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,
                       n_pairs: int) -> float:
     """Bytes each kernel must move per view (one pass over its inputs and outputs)."""
     px = C * H * W
-    lv, tail = mg_levels(H, W)
+    lv, t = mg_levels(H, W)
     if kernel == "mg0_down":   # r_k in; e, coarse rhs out
         return cycles * px * (4 + 4 + 1)
     if kernel == "mg0_up":     # r_k, e, coarse e in; u (hi, lo) out, r_{k+1} out; u in for k > 0
         return cycles * px * (4 + 4 + 1 + 8 + 4) + max(cycles - 1, 0) * px * 8
-    if kernel in ("mg_down", "mg_up"):  # levels 1 .. tail-1
+    if kernel in ("mg_down", "mg_up"):  # levels 1 .. t-1
         per = 4 + 4 + 1 if kernel == "mg_down" else 4 + 4 + 1 + 4
-        return cycles * sum(per * C * h * w for h, w in lv[1:tail])
+        return cycles * sum(per * C * h * w for h, w in lv[1:t])
+    if kernel == "mg_tail":    # f of level t in, u of level t out, the FP64 coarse inverse
+        nc = lv[-1][0] * lv[-1][1]
+        return cycles * C * (8 * lv[t][0] * lv[t][1] + 8 * nc * nc)
     if kernel == "divergence":  # maps in, rho out
         return px * (8 + 4)
     if kernel == "finalize":    # rho, u in; image out
@@ -320,6 +331,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "solver": {"nu1": sopts.nu1, "nu2": sopts.nu2, "omega": round(sopts.omega, 4),
+                                  "coarse_max_dim": sopts.coarse_max_dim, "rtol": rtol},
                        "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed views (256 MB write)"},
             "mpix_per_s": value * W * H / 1e6,

@@ -49,7 +49,7 @@ extern "C" {
 #define GDGS_API
 #endif
 
-#define GDGS_ABI_VERSION 1
+#define GDGS_ABI_VERSION 2
 #define GDGS_TILE 16        /* raster tile edge in pixels */
 #define GDGS_MAX_CHANNELS 4
 
@@ -123,14 +123,17 @@ typedef struct gdgs_raster_opts {
 /* Multigrid options (Sec. 2.1 lists multigrid among the linear-complexity
  * solvers; the paper fixes no parameters).
  *   nu1, nu2        red-black Gauss-Seidel sweeps before / after the coarse
- *                   correction, each in 1..3                         (2, 2)
+ *                   correction, each in 1..3                         (2, 1)
  *   max_cycles      upper bound on V-cycles, 1..64                   (30)
  *   rtol            stop when ||rho - L u||_2 <= rtol ||rho||_2       (1e-6)
  *   coarse_max_dim  coarsen until both grid sides are <= this; the
- *                   coarsest grid is solved directly in FP64, 2..16  (16)
+ *                   coarsest grid is solved directly in FP64, 2..16   (8)
  *   rho_threshold   t of the hard threshold T(x) = x if |x| >= t else 0
  *                   applied to the Laplacian field rho before the solve
- *                   (Eq. thresh); 0 keeps rho as it is                 (0) */
+ *                   (Eq. thresh); 0 keeps rho as it is                 (0)
+ *   omega           over-relaxation of the red-black Gauss-Seidel smoother,
+ *                   u <- u + omega (u_GS - u), in [0.5, 1.9]; it changes how
+ *                   fast the cycles converge, not what they converge to (1.2) */
 typedef struct gdgs_solver_opts {
   int32_t nu1;
   int32_t nu2;
@@ -138,6 +141,7 @@ typedef struct gdgs_solver_opts {
   float rtol;
   int32_t coarse_max_dim;
   float rho_threshold;
+  float omega;
 } gdgs_solver_opts;
 
 /* Filled by gdgs_sync_status() from the workspace after the stream has drained. */

@@ -11,7 +11,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libgdgs.so")
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 TILE = 16
 MAX_CHANNELS = 4
 
@@ -51,7 +51,7 @@ class RasterOpts(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", _i32), ("nu2", _i32), ("max_cycles", _i32), ("rtol", _f),
-                ("coarse_max_dim", _i32), ("rho_threshold", _f)]
+                ("coarse_max_dim", _i32), ("rho_threshold", _f), ("omega", _f)]
 
 
 class SolveStats(ctypes.Structure):

@@ -50,7 +50,7 @@ bool solver_opts_ok(const gdgs_solver_opts &o) {
   return o.nu1 >= 1 && o.nu1 <= 3 && o.nu2 >= 1 && o.nu2 <= 3 && o.max_cycles >= 1 &&
          o.max_cycles <= kMaxCycles && isfinite(o.rtol) && o.rtol >= 0.f &&
          o.coarse_max_dim >= 2 && o.coarse_max_dim <= 16 && isfinite(o.rho_threshold) &&
-         o.rho_threshold >= 0.f;
+         o.rho_threshold >= 0.f && o.omega >= 0.5f && o.omega <= 1.9f;
 }
 
 }  // namespace
@@ -87,7 +87,6 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
   p->levels = levels;
   for (int l = 0; l < levels; ++l) p->lv[l] = level_geom(H, W, l);
   p->nc = p->lv[levels - 1].H * p->lv[levels - 1].W;
-  p->tail = levels - 1;  // every level but the coarsest runs in the tiled kernels
 
   Carver cv;
   p->off_ctrl = cv.take(sizeof(Ctrl));
@@ -310,11 +309,12 @@ void gdgs_default_raster_opts(gdgs_raster_opts *o) {
 void gdgs_default_solver_opts(gdgs_solver_opts *o) {
   if (!o) return;
   o->nu1 = 2;
-  o->nu2 = 2;
+  o->nu2 = 1;
   o->max_cycles = 30;
   o->rtol = 1e-6f;
-  o->coarse_max_dim = 16;
+  o->coarse_max_dim = 8;
   o->rho_threshold = 0.f;
+  o->omega = 1.2f;
 }
 
 const char *gdgs_status_string(int s) {
@@ -414,6 +414,7 @@ static int poisson_common(const float *field, int input_is_rho, const uint8_t *t
   a.image = image;
   a.nu1 = so.nu1;
   a.nu2 = so.nu2;
+  a.omega = so.omega;
   a.max_cycles = so.max_cycles;
   a.rtol = so.rtol;
   a.plan = &p;
@@ -471,6 +472,7 @@ int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const floa
   a.image = image;
   a.nu1 = so.nu1;
   a.nu2 = so.nu2;
+  a.omega = so.omega;
   a.max_cycles = so.max_cycles;
   a.rtol = so.rtol;
   a.plan = &p;

@@ -91,7 +91,6 @@ struct Plan {
   size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1
   size_t off_coarse;                                   // tag + FP64 inverse
   int levels;         // number of levels (finest = 0, coarsest = levels-1)
-  int tail;           // = levels - 1 (levels below it run in the tiled kernels)
   int nc;             // unknowns on the coarsest level
   LevelGeom lv[kMaxLevels];
   size_t total;
@@ -183,6 +182,7 @@ struct PoissonArgs {
   float *image;             // [C][H][W]
   int nu1, nu2, max_cycles;
   float rtol;
+  float omega;              // smoother over-relaxation
   const Plan *plan;
   char *ws;
   Ctrl *ctrl;

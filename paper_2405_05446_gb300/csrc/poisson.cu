@@ -26,19 +26,21 @@
 // r_{k+1} = r_k - L e (r_0 = rho), whose norm decides convergence on the device.
 // The final iterate's residual rho - L u is recomputed in float-float arithmetic.
 //
-// Smoother and blocking. Red-black Gauss-Seidel. A CTA owns a 32 x 128 output
-// tile of a level, loads it with a halo of 2 nu + 1 rows (rounded up to 4 in x)
-// into shared memory and runs all sweeps there: every half-sweep shrinks the
-// valid region by one cell, and the halo absorbs that. Shared memory keeps the
-// even-x and odd-x cells of each row in separate planes, so the cells of one
-// colour in a row are contiguous and a half-sweep updates them four at a time
-// with 16-byte loads; work units away from the grid border take that path, the
-// few at the border a scalar path with the exact boundary coefficients. Down
-// kernels fuse the pre-sweeps with residual and restriction, up kernels the
-// prolongation with the post-sweeps (and, on the finest level, the update of u,
-// the new residual and its norm). Levels under kSmallLevel cells use 16 x 64
-// tiles. The coarsest grid is one FP64 matrix-vector product with the cached
-// inverse, one warp per row over many CTAs.
+// Smoother and blocking. Red-black Gauss-Seidel. On the large levels a CTA
+// owns a 32 x 128 output tile, loads it with a halo of 2 nu + 1 rows (rounded
+// up to 4 in x) into shared memory and runs all sweeps there: every half-sweep
+// shrinks the valid region by one cell, and the halo absorbs that. Shared
+// memory keeps the even-x and odd-x cells of each row in separate planes, so
+// the cells of one colour in a row are contiguous and a half-sweep updates them
+// four at a time with 16-byte loads; work units away from the grid border take
+// that path, the few at the border a scalar path with the exact boundary
+// coefficients. Down kernels fuse the pre-sweeps with residual and restriction,
+// up kernels the prolongation with the post-sweeps (and, on the finest level,
+// the update of u, the new residual and its norm). Levels under kSmallLevel
+// cells use 16 x 64 tiles. The levels from the first with at most kTailCells
+// cells per channel down to the coarsest run in one kernel, one CTA per
+// channel, entirely in shared memory; it also solves the coarsest grid with
+// the cached FP64 inverse.
 //
 // Convergence is decided on the device, so the cycle loop runs as a CUDA graph
 // with a WHILE node: no launch is spent after convergence.
@@ -281,7 +283,8 @@ __device__ __forceinline__ void build_factors(Factors<G> *fa, const LevelGeom &g
 // factor tables (cells outside the grid keep their value).
 template <class G>
 __device__ __forceinline__ void half_sweep(float *U, const float *F, const Factors<G> *fa,
-                                           const LevelGeom &g, int ry0, int rx0, int col) {
+                                           const LevelGeom &g, int ry0, int rx0, int col,
+                                           float omega) {
   constexpr int NU_ = (G::RY - 2) * G::NQ;
   const int tid = threadIdx.y * kBX + threadIdx.x;
   const int lane = threadIdx.x;
@@ -320,6 +323,13 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
       r.y = 0.25f * ((w1 + e1) + (up.y + dn.y) - f.y);
       r.z = 0.25f * ((w2 + e2) + (up.z + dn.z) - f.z);
       r.w = 0.25f * ((w3 + e3) + (up.w + dn.w) - f.w);
+      if (omega != 1.f) {  // u + omega (u_GS - u)
+        const float4 old = *reinterpret_cast<const float4 *>(Trow + m0);
+        r.x = fmaf(omega, r.x - old.x, old.x);
+        r.y = fmaf(omega, r.y - old.y, old.y);
+        r.z = fmaf(omega, r.z - old.z, old.z);
+        r.w = fmaf(omega, r.w - old.w, old.w);
+      }
     } else {
       const int pl = updE ? 0 : 1;
       const float wy = fa->wy[y], cS = fa->cS[y], cN = fa->cN[y];
@@ -333,6 +343,10 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
   }
       GDGS_CELL(x, w0, e0) GDGS_CELL(y, w1, e1) GDGS_CELL(z, w2, e2) GDGS_CELL(w, w3, e3)
 #undef GDGS_CELL
+      r.x = fmaf(omega, r.x - old.x, old.x);
+      r.y = fmaf(omega, r.y - old.y, old.y);
+      r.z = fmaf(omega, r.z - old.z, old.z);
+      r.w = fmaf(omega, r.w - old.w, old.w);
     }
     if (act) *reinterpret_cast<float4 *>(Trow + m0) = r;
   }
@@ -468,6 +482,7 @@ struct LvArgs {
   const float *rho;  // r_0
   float *rb[2];      // r_{k+1} is written to rb[k & 1]
   float *uhi, *ulo;  // float-float iterate
+  float omega;       // smoother over-relaxation
 };
 
 __device__ __forceinline__ const float *rhs_of(const LvArgs &a, int k) {
@@ -500,7 +515,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1);
+    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1, a.omega);
     __syncthreads();
   }
   float *uo = a.u + (size_t)c * g.plane;
@@ -536,7 +551,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 2 * NU; ++s) {
-    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1);
+    half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1, a.omega);
     __syncthreads();
   }
   if (!a.level0) {
@@ -597,27 +612,318 @@ struct UpShape {
       (2 * G::ARR + (G::CRY * G::CRX + 3) / 4 * 4) * sizeof(float) + sizeof(Factors<G>);
 };
 
-// ------------------------------------------------------------------ coarsest grid
+// ------------------------------------------------------------------ tail: the small levels in one CTA
+//
+// Levels t..L (t the first level >= 1 with at most kTailCells cells per
+// channel, L the coarsest) fit in one CTA's shared memory, so one CTA per
+// channel runs their whole part of the V-cycle: pre-sweeps, residual and
+// restriction from t down to L-1, the FP64 coarse solve on L, prolongation and
+// post-sweeps back up to t. Phases are separated by __syncthreads only. The
+// operator, transfers and sweep order are those of the tiled kernels (same
+// coef, residual and prolong1d), on the natural row-major layout.
 
-// u_L = Minv (-f_L) in FP64 on the coarsest grid: one warp per row of the cached
-// inverse, rows spread over many CTAs (the dense product is the whole solve).
-__global__ void __launch_bounds__(256)
-coarse_solve_kernel(const double *__restrict__ Minv, int nc, const float *__restrict__ f,
-                    float *u, long long plane, Ctrl *ctrl, int k_in, int first) {
+constexpr long long kTailCells = 12288;
+constexpr int kTailThreads = 1024;
+
+struct TailArgs {
+  LevelGeom lv[kMaxLevels];  // lv[i] = level t + i; lv[n - 1] is the coarsest
+  int off_u[kMaxLevels];     // shared-memory float offsets: u of level i (f follows)
+  int off_t[kMaxLevels];     // and its row / column tables
+  int off_minv;              // the staged coarse inverse (doubles), or -1: read from global
+  int off_fd;                // -f of the coarsest level in FP64
+  int n;                     // levels in the tail (>= 1)
+  const float *f_top;        // right-hand side of level t [C][plane]
+  float *u_top;              // correction of level t [C][plane] (output)
+  const double *Minv;        // [nc][nc] inverse of -L + 11^T / nc on the coarsest level
+  int nu1, nu2;
+  float omega;
+};
+
+__host__ __device__ __forceinline__ int tail_stride(const LevelGeom &g) {
+  return (int)((g.plane + 3) & ~3ll);
+}
+
+// Shared-memory layout of the tail: u and f of every level, then per level the
+// row tables (H entries each: wy, cS, cN, and the prolongation rows i0, i1, w
+// from the next coarser level) and the column tables (W entries each: wx, cE,
+// cW, i0, i1, w), then (for small coarsest grids) the FP64 inverse. A cell's
+// face coefficients are products of one row and one column factor (e = wy cE,
+// w = wy cW, s = wx cS, n = wx cN), so every sweep, residual and prolongation
+// is branch-free. Offsets are computed on the host.
+constexpr int kTailMinvStage = 64;  // stage the inverse when nc <= this
+
+inline size_t tail_layout(const LevelGeom *lv, int n, TailArgs *a) {
+  size_t o = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a) a->off_u[i] = (int)o;
+    o += 2 * (size_t)tail_stride(lv[i]);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (a) a->off_t[i] = (int)o;
+    o += 6 * (size_t)(lv[i].H + lv[i].W);
+  }
+  const long long nc = lv[n - 1].plane;
+  o = (o + 1) & ~(size_t)1;  // 8-byte alignment for the doubles
+  if (a) a->off_fd = (int)o;
+  o += 2 * (size_t)nc;
+  if (nc <= kTailMinvStage) {
+    if (a) a->off_minv = (int)o;
+    o += 2 * (size_t)(nc * nc);
+  } else if (a) {
+    a->off_minv = -1;
+  }
+  return o;
+}
+
+struct TailLevel {
+  int H, W;
+  float *u, *f;
+  const float *wy, *cS, *cN, *wx, *cE, *cW;
+  const int *ri0, *ri1, *ci0, *ci1;
+  const float *rw, *cw;
+};
+
+__device__ __forceinline__ TailLevel tail_level_at(float *S, const TailArgs &a, int i) {
+  TailLevel t;
+  t.H = a.lv[i].H;
+  t.W = a.lv[i].W;
+  t.u = S + a.off_u[i];
+  t.f = t.u + tail_stride(a.lv[i]);
+  float *R = S + a.off_t[i], *Cc = R + 6 * t.H;
+  t.wy = R;
+  t.cS = R + t.H;
+  t.cN = R + 2 * t.H;
+  t.ri0 = reinterpret_cast<const int *>(R + 3 * t.H);
+  t.ri1 = reinterpret_cast<const int *>(R + 4 * t.H);
+  t.rw = R + 5 * t.H;
+  t.wx = Cc;
+  t.cE = Cc + t.W;
+  t.cW = Cc + 2 * t.W;
+  t.ci0 = reinterpret_cast<const int *>(Cc + 3 * t.W);
+  t.ci1 = reinterpret_cast<const int *>(Cc + 4 * t.W);
+  t.cw = Cc + 5 * t.W;
+  return t;
+}
+
+// Row and column tables of every tail level (the same factors as build_factors).
+__device__ void tail_build_tables(float *S, const TailArgs &a) {
+  for (int i = 0; i < a.n; ++i) {
+    const LevelGeom &g = a.lv[i];
+    const TailLevel t = tail_level_at(S, a, i);
+    float *R = const_cast<float *>(t.wy), *Cc = const_cast<float *>(t.wx);
+    const bool has_c = i + 1 < a.n;
+    for (int k = threadIdx.x; k < t.H + t.W; k += kTailThreads) {
+      const bool row = k < t.H;
+      const int r = row ? k : k - t.H, n = row ? t.H : t.W;
+      const float last = row ? g.ey : g.ex;
+      float *T = row ? R : Cc;
+      T[r] = row ? wyf(g, r) : wxf(g, r);
+      T[n + r] = r + 1 < n ? (r + 1 == n - 1 ? last : 1.f) : 0.f;  // cS / cE
+      T[2 * n + r] = r > 0 ? (r == n - 1 ? last : 1.f) : 0.f;      // cN / cW
+      P1 p{r >> 1, r >> 1, 0.f};
+      if (has_c) {
+        const LevelGeom &gc = a.lv[i + 1];
+        p = row ? prolong1d(r, g.shift, g.H0, gc.H) : prolong1d(r, g.shift, g.W0, gc.W);
+      }
+      reinterpret_cast<int *>(T)[3 * n + r] = p.i0;
+      reinterpret_cast<int *>(T)[4 * n + r] = p.i1;
+      T[5 * n + r] = p.w1;
+    }
+  }
+}
+
+// Gauss-Seidel value of cell (I, J) from its neighbours, with the row factors
+// of row I (wy, cS, cN) and the column tables.
+__device__ __forceinline__ float tail_gs(const TailLevel &t, const float *ur, const float *fr,
+                                         int I, int J, float wy, float cS, float cN) {
+  const int W = t.W;
+  const float wx = t.wx[J];
+  const float ae = wy * t.cE[J], aw = wy * t.cW[J], as = wx * cS, an = wx * cN;
+  const float uE = J + 1 < W ? ur[J + 1] : 0.f;
+  const float uW = J > 0 ? ur[J - 1] : 0.f;
+  const float uS = I + 1 < t.H ? ur[J + W] : 0.f;
+  const float uN = I > 0 ? ur[J - W] : 0.f;
+  const float d = (ae + aw) + (as + an);
+  return __fdividef((ae * uE + aw * uW) + (as * uS + an * uN) - fr[J], d);
+}
+
+// One red-black half-sweep over the cells with (I + J) & 1 == col; a warp per
+// row, two cells of the row per lane and iteration (loads first). With
+// from_zero (the first pre-sweep of a level) the other cells are set to 0
+// instead of being read, so u needs no clearing pass.
+__device__ __forceinline__ void tail_half_sweep(const TailLevel &t, int col, bool from_zero,
+                                                float omega) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = t.H, W = t.W;
+  for (int I = warp; I < H; I += kTailThreads / 32) {
+    const float wy = t.wy[I], cS = t.cS[I], cN = t.cN[I];
+    float *ur = t.u + I * W;
+    const float *fr = t.f + I * W;
+    if (from_zero) {
+      for (int J = lane; J < W; J += 32) {
+        float v = 0.f;
+        if (((I + J) & 1) == col) {
+          const float d = wy * (t.cE[J] + t.cW[J]) + t.wx[J] * (cS + cN);
+          v = omega * __fdividef(-fr[J], d);
+        }
+        ur[J] = v;
+      }
+      continue;
+    }
+    for (int J0 = 2 * lane + ((I + col) & 1); J0 < W; J0 += 128) {
+      const int J1 = J0 + 64;
+      const bool two = J1 < W;
+      const float g0 = tail_gs(t, ur, fr, I, J0, wy, cS, cN);
+      const float g1 = two ? tail_gs(t, ur, fr, I, J1, wy, cS, cN) : 0.f;
+      const float o0 = ur[J0], o1 = two ? ur[J1] : 0.f;
+      ur[J0] = fmaf(omega, g0 - o0, o0);
+      if (two) ur[J1] = fmaf(omega, g1 - o1, o1);
+    }
+  }
+}
+
+__device__ __forceinline__ float tail_residual(const TailLevel &t, int I, int J, float wy, float cS,
+                                               float cN) {
+  const int W = t.W, q = I * W + J;
+  const float u = t.u[q], wx = t.wx[J];
+  const float dE = J + 1 < W ? t.u[q + 1] - u : 0.f;
+  const float dW = J > 0 ? t.u[q - 1] - u : 0.f;
+  const float dS = I + 1 < t.H ? t.u[q + W] - u : 0.f;
+  const float dN = I > 0 ? t.u[q - W] - u : 0.f;
+  return t.f[q] - ((wy * t.cE[J] * dE + wy * t.cW[J] * dW) + (wx * cS * dS + wx * cN * dN));
+}
+
+__global__ void __launch_bounds__(kTailThreads)
+mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
+  extern __shared__ float4 sm4[];
+  float *S = reinterpret_cast<float *>(sm4);
   const int k = cycle_index(ctrl, k_in);
   if (should_stop(ctrl, k, first)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + warp;
-  if (row >= nc) return;  // whole warp
-  const int c = blockIdx.y;
-  const float *fc = f + (size_t)c * plane;
-  const double *mr = Minv + (size_t)row * nc;
-  double acc = 0.0;
-#pragma unroll 4
-  for (int j = lane; j < nc; j += 32) acc = fma(__ldg(mr + j), -(double)__ldg(fc + j), acc);
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kWarps = kTailThreads / 32;
+
+  {  // right-hand side of the top level and the coarse inverse: loads first
+    const TailLevel t = tail_level_at(S, a, 0);
+    const float *src = a.f_top + (size_t)c * a.lv[0].plane;
+    const int np = (int)a.lv[0].plane;
+    for (int q0 = tid; q0 < np; q0 += 4 * kTailThreads) {
+      float v[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) u[(size_t)c * plane + row] = (float)acc;
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + j * kTailThreads;
+        v[j] = q < np ? __ldg(src + q) : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + j * kTailThreads;
+        if (q < np) t.f[q] = v[j];
+      }
+    }
+    if (a.off_minv >= 0) {
+      const int nc = (int)a.lv[a.n - 1].plane, n2 = nc * nc;
+      double *M = reinterpret_cast<double *>(S + a.off_minv);
+      for (int q0 = tid; q0 < n2; q0 += 4 * kTailThreads) {
+        double v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = q0 + j * kTailThreads;
+          v[j] = q < n2 ? __ldg(a.Minv + q) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = q0 + j * kTailThreads;
+          if (q < n2) M[q] = v[j];
+        }
+      }
+    }
+    tail_build_tables(S, a);
+    __syncthreads();
+  }
+  for (int i = 0; i + 1 < a.n; ++i) {  // down: sweeps from 0, restrict the residual
+    const TailLevel t = tail_level_at(S, a, i), tc = tail_level_at(S, a, i + 1);
+    for (int s = 0; s < 2 * a.nu1; ++s) {
+      tail_half_sweep(t, s & 1, s == 0, a.omega);
+      __syncthreads();
+    }
+    for (int CI = warp; CI < tc.H; CI += kWarps) {
+      const int I = 2 * CI;
+      const bool two = I + 1 < t.H;
+      const float wy0 = t.wy[I], cS0 = t.cS[I], cN0 = t.cN[I];
+      const float wy1 = two ? t.wy[I + 1] : 0.f, cS1 = two ? t.cS[I + 1] : 0.f,
+                  cN1 = two ? t.cN[I + 1] : 0.f;
+      for (int CJ = lane; CJ < tc.W; CJ += 32) {
+        const int J = 2 * CJ;
+        float sum = tail_residual(t, I, J, wy0, cS0, cN0);
+        if (J + 1 < t.W) sum += tail_residual(t, I, J + 1, wy0, cS0, cN0);
+        if (two) {
+          sum += tail_residual(t, I + 1, J, wy1, cS1, cN1);
+          if (J + 1 < t.W) sum += tail_residual(t, I + 1, J + 1, wy1, cS1, cN1);
+        }
+        tc.f[CI * tc.W + CJ] = sum;
+      }
+    }
+    __syncthreads();
+  }
+  {  // coarsest: u = Minv (-f) in FP64; one thread per row, four partial sums
+    const TailLevel t = tail_level_at(S, a, a.n - 1);
+    const int nc = t.H * t.W;
+    const double *M = a.off_minv >= 0 ? reinterpret_cast<const double *>(S + a.off_minv) : a.Minv;
+    double *fd = reinterpret_cast<double *>(S + a.off_fd);
+    for (int j = tid; j < nc; j += kTailThreads) fd[j] = -(double)t.f[j];
+    __syncthreads();
+    for (int row = tid; row < nc; row += kTailThreads) {
+      const double *mr = M + (size_t)row * nc;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < nc; j += 4) {
+        s0 = fma(mr[j], fd[j], s0);
+        s1 = fma(mr[j + 1], fd[j + 1], s1);
+        s2 = fma(mr[j + 2], fd[j + 2], s2);
+        s3 = fma(mr[j + 3], fd[j + 3], s3);
+      }
+      for (; j < nc; ++j) s0 = fma(mr[j], fd[j], s0);
+      t.u[row] = (float)((s0 + s1) + (s2 + s3));
+    }
+    __syncthreads();
+  }
+  for (int i = a.n - 2; i >= 0; --i) {  // up: prolongate the correction, post-sweeps
+    const TailLevel t = tail_level_at(S, a, i), tc = tail_level_at(S, a, i + 1);
+    for (int I = warp; I < t.H; I += kWarps) {
+      const float *ra = tc.u + t.ri0[I] * tc.W, *rb = tc.u + t.ri1[I] * tc.W;
+      const float wr = t.rw[I];
+      float *ur = t.u + I * t.W;
+      for (int J0 = lane; J0 < t.W; J0 += 128) {  // four columns per lane: loads first
+        float add[4], cur[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int J = J0 + 32 * k;
+          add[k] = cur[k] = 0.f;
+          if (J < t.W) {
+            const int j0 = t.ci0[J], j1 = t.ci1[J];
+            const float wc = t.cw[J];
+            const float a0 = ra[j0] + wc * (ra[j1] - ra[j0]);
+            const float a1 = rb[j0] + wc * (rb[j1] - rb[j0]);
+            add[k] = a0 + wr * (a1 - a0);
+            cur[k] = ur[J];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (J0 + 32 * k < t.W) ur[J0 + 32 * k] = cur[k] + add[k];
+      }
+    }
+    __syncthreads();
+    for (int s = 0; s < 2 * a.nu2; ++s) {
+      tail_half_sweep(t, s & 1, false, a.omega);
+      __syncthreads();
+    }
+  }
+  {
+    const TailLevel t = tail_level_at(S, a, 0);
+    float *dst = a.u_top + (size_t)c * a.lv[0].plane;
+    for (int q = tid; q < a.lv[0].plane; q += kTailThreads) dst[q] = t.u[q];
+  }
 }
 
 // ------------------------------------------------------------------ setup, divergence, finalize
@@ -640,7 +946,9 @@ __device__ unsigned long long digest(const double *A, int n2) {
   unsigned long long h = 0;
   for (int i = threadIdx.x; i < n2; i += blockDim.x)
     h += mix64((unsigned long long)__double_as_longlong(A[i]) ^ (0x9e3779b97f4a7c15ull * (i + 1)));
-  atomicAdd(&acc, h);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&acc, h);  // one shared atomic per warp
   __syncthreads();
   return acc;
 }
@@ -911,12 +1219,29 @@ cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t
                           : launch_mg_up_t<NU, 32, 128>(a, ctrl, k, C, st);
 }
 
-// Everything one V-cycle launches, for workspace `ws` laid out by `p`.
+inline size_t tail_smem(const Plan &p, int t) {
+  return tail_layout(p.lv + t, p.levels - t, nullptr) * sizeof(float);
+}
+
+// First level of the tail kernel: the first level >= 1 with at most kTailCells
+// cells per channel whose tail fits kTailSmemMax bytes of shared memory (only
+// very elongated grids need a later one; the coarsest alone always fits).
+constexpr size_t kTailSmemMax = 200 * 1024;
+
+inline int tail_level(const Plan &p) {
+  int t = 1;
+  while (t < p.levels - 1 && (p.lv[t].plane > kTailCells || tail_smem(p, t) > kTailSmemMax)) ++t;
+  return t;
+}
+
+// Everything one V-cycle launches, for workspace `ws` laid out by `p`: the
+// tiled levels 0 .. t-1 down, the tail (levels t .. L), the tiled levels up.
 struct Cycle {
   const Plan *p;
   char *ws;
   Ctrl *ctrl;
   int C, nu1, nu2;
+  float omega;
   const double *Minv;
 
   LvArgs level(int l) const {
@@ -933,10 +1258,26 @@ struct Cycle {
     a.rb[1] = (float *)(ws + p->off_r[1]);
     a.uhi = (float *)(ws + p->off_uhi);
     a.ulo = (float *)(ws + p->off_ulo);
+    a.omega = omega;
     return a;
   }
-  int L() const { return p->levels - 1; }
-  unsigned kernels() const { return 2u * (unsigned)L() + 2u; }
+  int T() const { return tail_level(*p); }
+  unsigned kernels() const { return 2u * (unsigned)T() + 2u; }
+
+  TailArgs tail() const {
+    TailArgs a{};
+    const int t = T();
+    a.n = p->levels - t;
+    for (int i = 0; i < a.n; ++i) a.lv[i] = p->lv[t + i];
+    tail_layout(a.lv, a.n, &a);
+    a.f_top = (const float *)(ws + p->off_lf[t]);
+    a.u_top = (float *)(ws + p->off_lu[t]);
+    a.Minv = Minv;
+    a.nu1 = nu1;
+    a.nu2 = nu2;
+    a.omega = omega;
+    return a;
+  }
 
   // Opt-in to large dynamic shared memory for every kernel of the cycle; done
   // before any capture (attributes are set once per kernel and device).
@@ -946,6 +1287,7 @@ struct Cycle {
     if (e == cudaSuccess) e = set_smem<mg_down_kernel<A, 16, 64>>(DownShape<Geo<A, 16, 64>>::smem);
     if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 32, 128>>(UpShape<Geo<B, 32, 128>>::smem);
     if (e == cudaSuccess) e = set_smem<mg_up_kernel<B, 16, 64>>(UpShape<Geo<B, 16, 64>>::smem);
+    if (e == cudaSuccess) e = set_smem<mg_tail_kernel>(tail_smem(*p, T()));
     return e;
   }
   cudaError_t prepare() const {
@@ -961,7 +1303,8 @@ struct Cycle {
   // k >= 0: explicit cycle index; k < 0: read from ctrl->iter (graph body).
   cudaError_t launch(int k, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) const {
     cudaError_t e = cudaSuccess;
-    for (int l = 0; l < L(); ++l) {
+    const int t = T();
+    for (int l = 0; l < t; ++l) {
       const LvArgs la = level(l);
       const int first = (l == 1);
       e = nu1 == 1 ? launch_mg_down<1>(la, ctrl, k, first, C, st)
@@ -970,15 +1313,11 @@ struct Cycle {
       if (e != cudaSuccess) return e;
     }
     {
-      const LevelGeom &gc = p->lv[L()];
-      const dim3 grid((p->nc + 7) / 8, C);
-      LaunchScope ls_("mg_coarse", st);
-      coarse_solve_kernel<<<grid, 256, 0, st>>>(Minv, p->nc, (const float *)(ws + p->off_lf[L()]),
-                                                (float *)(ws + p->off_lu[L()]), gc.plane, ctrl, k,
-                                                L() == 1 ? 1 : 0);
+      LaunchScope ls_("mg_tail", st);
+      mg_tail_kernel<<<C, kTailThreads, tail_smem(*p, t), st>>>(tail(), ctrl, k, t == 1 ? 1 : 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    for (int l = L() - 1; l >= 0; --l) {
+    for (int l = t - 1; l >= 0; --l) {
       const LvArgs la = level(l);
       e = nu2 == 1 ? launch_mg_up<1>(la, ctrl, k, C, st)
           : nu2 == 2 ? launch_mg_up<2>(la, ctrl, k, C, st)
@@ -1005,11 +1344,12 @@ struct GraphKey {
   int dev;
   const void *ws;
   int C, H, W, nu1, nu2, max_cycles, levels;
+  float omega;
   size_t off_rho, off_coarse, total;
   bool operator<(const GraphKey &o) const {
-    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, off_rho, off_coarse, total) <
-           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.levels, o.off_rho,
-                    o.off_coarse, o.total);
+    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, omega, off_rho, off_coarse,
+                    total) < std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles,
+                                      o.levels, o.omega, o.off_rho, o.off_coarse, o.total);
   }
 };
 
@@ -1149,6 +1489,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   cy.C = a.C;
   cy.nu1 = a.nu1;
   cy.nu2 = a.nu2;
+  cy.omega = a.omega;
   cy.Minv = Minv;
 
   if ((e = cy.prepare()) != cudaSuccess) return e;
@@ -1157,8 +1498,8 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const GraphKey key{dev, ws, a.C, a.H, a.W, a.nu1, a.nu2, a.max_cycles, p.levels,
-                       p.off_rho, p.off_coarse, p.total};
+    const GraphKey key{dev,      ws,         a.C,    a.H,     a.W,       a.nu1, a.nu2,
+                       a.max_cycles, p.levels, a.omega, p.off_rho, p.off_coarse, p.total};
     if ((e = launch_cycle_graph(cy, key, st)) != cudaSuccess) return e;
   } else {
     // direct launches: every cycle is enqueued; once the advance kernel has

@@ -50,7 +50,7 @@ def test_abi_version_and_defaults(lib):
     assert r.t_min == pytest.approx(1e-4) and r.exp_coef == 1.0 and r.pairs_per_gaussian == 16
     s = _abi.SolverOpts()
     lib.gdgs_default_solver_opts(s)
-    assert (s.nu1, s.nu2, s.coarse_max_dim) == (2, 2, 16) and s.rtol == pytest.approx(1e-6)
+    assert (s.nu1, s.nu2, s.coarse_max_dim) == (2, 1, 8) and s.rtol == pytest.approx(1e-6)
     for code in range(8):
         assert lib.gdgs_status_string(code)
     assert lib.gdgs_status_string(99) == b"unknown status"
@@ -60,7 +60,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_abi.Gaussians) == 8 + 4 + 4 + 5 * 8
     assert ctypes.sizeof(_abi.Camera) == 17 * 4 + 8
     assert ctypes.sizeof(_abi.RasterOpts) == 24
-    assert ctypes.sizeof(_abi.SolverOpts) == 24
+    assert ctypes.sizeof(_abi.SolverOpts) == 28
     assert ctypes.sizeof(_abi.SolveStats) == 4 + 4 + 8 + 8 + 32 + 8 + 4 + 4
 
 

@@ -153,6 +153,23 @@ def test_poisson_matches_dct_oracle(hw):
     np.testing.assert_allclose(img.mean(axis=(1, 2)), mean, atol=1e-6)
 
 
+@pytest.mark.parametrize("hw", [(2, 12000), (12000, 2)])
+def test_poisson_long_strip(hw):
+    """Strips whose small levels do not fit the one-CTA tail with their coefficient
+    tables (the tail then starts one level lower): the FP64 residual of the image
+    and its mean, checked against the Neumann Laplacian of Eq. p2d."""
+    rng = np.random.default_rng(hw[0])
+    H, W = hw
+    img0 = rng.random((1, H, W))
+    maps = O.forward_gradients(img0)
+    rho = O.divergence(maps)
+    img, st = gpu_poisson(maps.astype(np.float32), [0.5])
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    r = rho - O.laplacian_neumann(img)
+    assert np.linalg.norm(r) <= 2e-6 * np.linalg.norm(rho)
+    assert abs(img.mean() - 0.5) <= 1e-6
+
+
 def test_poisson_recovers_known_image_1080p():
     H, W = 1080, 1920
     img0 = np.stack([S.image_from_gradients_test_image(H, W, seed=s) for s in range(3)])
@@ -337,17 +354,44 @@ def test_graph_cache_distinguishes_workspace_layouts():
 
 @pytest.mark.parametrize("coarse", [2, 16])
 @pytest.mark.parametrize("nu", [(1, 1), (3, 2)])
-def test_poisson_solver_options(coarse, nu):
-    """Other coarsest-grid sizes (down to 2x2, up to 16x16) and sweep counts reach
-    the same solution."""
+@pytest.mark.parametrize("omega", [1.0, 1.2])
+def test_poisson_solver_options(coarse, nu, omega):
+    """Other coarsest-grid sizes (down to 2x2, up to 16x16), sweep counts and
+    smoother relaxations reach the same solution."""
     rng = np.random.default_rng(coarse * 10 + nu[0])
     H, W = 150, 211
     maps = rng.laplace(0, 0.1, (2, 2, H, W)).astype(np.float32)
-    so = G.solver_opts(coarse_max_dim=coarse, nu1=nu[0], nu2=nu[1])
+    so = G.solver_opts(coarse_max_dim=coarse, nu1=nu[0], nu2=nu[1], omega=omega)
     img, st = gpu_poisson(maps, [0.5, 0.5], so)
     ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), [0.5, 0.5])
     assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
     assert img_err(img, ref)[0] <= IMG_TOL
+
+
+def test_relaxation_changes_speed_not_the_answer():
+    """omega = 1 (plain Gauss-Seidel) and omega = 1.2 give images that agree to the
+    solver tolerance; with one workspace, the graph cache keeps the two apart."""
+    rng = np.random.default_rng(21)
+    C, H, W = 3, 270, 480
+    maps = torch.as_tensor(rng.laplace(0, 0.1, (C, 2, H, W)).astype(np.float32)).cuda()
+    ws = torch.empty(G.workspace_size(0, C, W, H, None, None), dtype=torch.uint8, device="cuda")
+
+    def solve(omega):
+        img = torch.empty((C, H, W), device="cuda")
+        G.poisson_reconstruct(maps, [0.5] * C, img, ws, sopts=G.solver_opts(omega=omega))
+        st = G.sync_status(ws)
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+        return img.cpu().numpy().astype(np.float64), st["cycles"]
+
+    i1, k1 = solve(1.0)
+    i2, k2 = solve(1.2)
+    i3, k3 = solve(1.0)
+    assert k2 <= k1 == k3
+    assert np.array_equal(i1, i3)
+    assert not np.array_equal(i1, i2)  # a stale graph would have repeated omega = 1
+    assert np.abs(i1 - i2).max() <= IMG_TOL
+    ref = O.poisson_neumann(O.divergence(maps.cpu().numpy().astype(np.float64)), [0.5] * C)
+    assert img_err(i2, ref)[0] <= IMG_TOL
 
 
 def test_coarse_factor_cache_survives_other_layouts_and_detects_corruption():
