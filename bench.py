@@ -137,6 +137,30 @@ def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss:
     return 0.0
 
 
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from an ncu summary under profiles/ (its
+    `bench-traffic:` line), or None when none exists or the kernel's source file
+    has changed since the counters were taken (the line records its SHA-256)."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("bench-traffic:"):
+                continue
+            kv = dict(item.split("=", 1) for item in line.split(":", 1)[1].split())
+            if kv.get("kernel") != kernel:
+                continue
+            src = os.path.join(ROOT, kv["source"])
+            if not os.path.exists(src):
+                return None
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            if sha != kv.get("source_sha256"):
+                return None
+            return {"bytes_per_launch": float(kv["bytes_per_launch"]), "cycle": kv.get("cycle"),
+                    "summary": os.path.relpath(path, ROOT)}
+    return None
+
+
 def make_workload(name):
     from paper_2405_05446_gb300 import scenes as S
     return S.workload(name)
@@ -319,10 +343,16 @@ def main():
         per_kernel_roof[k] = round(b_ / (kernels[k]["ms_per_view"] / 1e3) / 1e9 / hbm, 4)
     nbytes = algorithmic_bytes(roof_k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
     ms = kernels[roof_k]["ms_per_view"]
+    launches_pv = kernels[roof_k]["launches_per_view"]
     achieved = nbytes / (ms / 1e3) / 1e9
+    tr = profiled_traffic(roof_k)
     roofline = {"bound": "hbm", "kernel": roof_k, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                "algorithmic_bytes_per_view": nbytes, "traffic": None,
+                "algorithmic_bytes_per_launch": nbytes / max(launches_pv, 1.0),
+                "avg_launch_ms": ms / max(launches_pv, 1.0),
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_source": tr,
+                "algorithmic_bytes_per_view": nbytes,
                 "dominant_kernel": dom, "dominant_share": kernels[dom]["share"],
                 "frac_by_kernel": per_kernel_roof}
 

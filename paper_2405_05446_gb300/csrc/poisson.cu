@@ -199,11 +199,22 @@ struct Geo {
   static constexpr int ARR = 2 * PLANE;
   static constexpr int CRY = RY / 2 + 4, CRX = RXP / 2 + 4;  // coarse box bound
   static_assert(RXP % 8 == 0 && S % 4 == 0 && PLANE % 4 == 0 && CRX % 4 == 0, "quad alignment");
+  static_assert(HX % 4 == 0 && TX % 8 == 0 && (TY * TX / 4) % (kBX * kBY) == 0, "vector paths");
 };
 
 template <class G>
 __device__ __forceinline__ float &at(float *A, int y, int x) {
   return A[(x & 1) * G::PLANE + y * G::S + 4 + (x >> 1)];
+}
+
+template <class G>
+__device__ __forceinline__ void zero_pads(float *A) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int i = tid; i < 2 * G::RY * 8; i += kMgThreads) {
+    const int plane = i / (G::RY * 8), r = i % (G::RY * 8);
+    const int y = r >> 3, j = r & 7;
+    A[plane * G::PLANE + y * G::S + (j < 4 ? j : G::NC + j)] = 0.f;
+  }
 }
 
 // Loads src (a level array) into the split layout; cells outside the grid read 0.
@@ -230,13 +241,77 @@ __device__ __forceinline__ void load_split(float *A, const float *__restrict__ s
       const int y = threadIdx.y + kBY * i, x = threadIdx.x + kBX * j;
       if (y < G::RY && x < G::RXP) at<G>(A, y, x) = v[i][j];
     }
-  // pad slots
+  zero_pads<G>(A);
+}
+
+// The same with 16-byte loads, for W % 4 == 0: rx0 is a multiple of 4 too, so
+// every group of 4 cells is wholly inside or outside the grid. A group (x, x+1,
+// x+2, x+3) goes to the even plane as (x, x+2) and to the odd one as (x+1, x+3).
+template <class G>
+__device__ __forceinline__ void load_split4(float *A, const float *__restrict__ src,
+                                            const LevelGeom &g, int ry0, int rx0, float off) {
+  constexpr int NG = G::RXP / 4, TOT = G::RY * NG;
+  constexpr int PER = (TOT + kMgThreads - 1) / kMgThreads;
   const int tid = threadIdx.y * kBX + threadIdx.x;
-  for (int i = tid; i < 2 * G::RY * 8; i += kMgThreads) {
-    const int plane = i / (G::RY * 8), r = i % (G::RY * 8);
-    const int y = r >> 3, j = r & 7;
-    A[plane * G::PLANE + y * G::S + (j < 4 ? j : G::NC + j)] = 0.f;
+  float4 v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * kMgThreads;
+    const int y = idx / NG, q = idx - y * NG;
+    const int gy = ry0 + y, gx = rx0 + 4 * q;
+    const bool in = idx < TOT && gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
+    v[i] = in ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)gy * g.W + gx))
+              : make_float4(off, off, off, off);
   }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * kMgThreads;
+    if (idx < TOT) {
+      const int y = idx / NG, q = idx - y * NG;
+      float *row = A + y * G::S + 4 + 2 * q;
+      *reinterpret_cast<float2 *>(row) = make_float2(v[i].x - off, v[i].z - off);
+      *reinterpret_cast<float2 *>(row + G::PLANE) = make_float2(v[i].y - off, v[i].w - off);
+    }
+  }
+  zero_pads<G>(A);
+}
+
+// 16-byte paths need rows that start on 16 bytes: W % 4 == 0 (channel planes
+// are then 16-byte multiples as well; level arrays are 256-byte aligned).
+__device__ __forceinline__ bool vec4_ok(const LevelGeom &g) { return (g.W & 3) == 0; }
+
+template <class G>
+__device__ __forceinline__ void load_tile(float *A, const float *__restrict__ src,
+                                          const LevelGeom &g, int ry0, int rx0, float off = 0.f) {
+  if (vec4_ok(g)) load_split4<G>(A, src, g, ry0, rx0, off);
+  else load_split<G>(A, src, g, ry0, rx0, off);
+}
+
+// Writes the output tile (region rows HY.., columns HX..) of U to dst.
+template <class G>
+__device__ __forceinline__ void store_tile(const float *U, float *dst, const LevelGeom &g, int ty0,
+                                           int tx0) {
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  if (vec4_ok(g)) {
+    constexpr int NG = G::TX / 4, TOT = G::TY * NG;
+#pragma unroll
+    for (int i = 0; i < TOT / kMgThreads; ++i) {
+      const int idx = tid + i * kMgThreads;
+      const int y = idx / NG, q = idx - y * NG;
+      const int gy = ty0 + y, gx = tx0 + 4 * q;
+      if (gy >= g.H || gx >= g.W) continue;
+      const float *row = U + (y + G::HY) * G::S + 4 + ((4 * q + G::HX) >> 1);
+      const float2 e = *reinterpret_cast<const float2 *>(row);
+      const float2 o = *reinterpret_cast<const float2 *>(row + G::PLANE);
+      *reinterpret_cast<float4 *>(dst + (size_t)gy * g.W + gx) = make_float4(e.x, o.x, e.y, o.y);
+    }
+    return;
+  }
+  for (int y = threadIdx.y; y < G::TY; y += kBY)
+    for (int x = threadIdx.x; x < G::TX; x += kBX) {
+      const int gy = ty0 + y, gx = tx0 + x;
+      if (gy < g.H && gx < g.W) dst[(size_t)gy * g.W + gx] = at<G>(const_cast<float *>(U), y + G::HY, x + G::HX);
+    }
 }
 
 template <class G>
@@ -318,7 +393,8 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
                 e3 = updE ? qv.w : qx;
     const int gx0 = rx0 + 2 * m0;
     float4 r;
-    if (gy >= 1 && gy <= g.H - 3 && gx0 >= 1 && gx0 + 7 <= g.W - 3) {
+    const bool fast = gy >= 1 && gy <= g.H - 3 && gx0 >= 1 && gx0 + 7 <= g.W - 3;
+    if (__all_sync(0xffffffffu, fast || !act)) {  // warp-uniform: no predicated border path
       r.x = 0.25f * ((w0 + e0) + (up.x + dn.x) - f.x);
       r.y = 0.25f * ((w1 + e1) + (up.y + dn.y) - f.y);
       r.z = 0.25f * ((w2 + e2) + (up.z + dn.z) - f.z);
@@ -361,30 +437,72 @@ __device__ __forceinline__ float tile_residual(float *U, float *F, const LevelGe
 }
 
 // Sum of the four children's residuals for each coarse cell under the output
-// tile (ty0, tx0) -> fc. Thread (tx, ty) owns coarse columns tx, tx + 32 and
-// rows ty, ty + 8.
+// tile (ty0, tx0) -> fc. A work unit is a pair of coarse cells (fine columns
+// J .. J+3 of rows I, I+1); away from the border (warp-uniform test) its eight
+// residuals come from 8-byte loads of the split planes, elsewhere from the
+// general cell formula.
 template <class G>
 __device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeom &g,
                                               const LevelGeom &gc, int ty0, int tx0, float *fc) {
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
-  static_assert(G::TY / 2 % kBY == 0 && G::TX / 2 % kBX == 0, "tile vs threads");
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  constexpr int CW2 = G::TX / 4, NP = (G::TY / 2) * CW2;
+  static_assert(NP % 32 == 0, "whole warps per pass");
 #pragma unroll
-  for (int i = 0; i < G::TY / 2 / kBY; ++i)
+  for (int i = 0; i < (NP + kMgThreads - 1) / kMgThreads; ++i) {
+    const int idx = tid + i * kMgThreads;
+    if (idx >= NP) break;  // whole warps
+    const int cy = idx / CW2, cq = idx - cy * CW2;
+    const int CI = (ty0 >> 1) + cy, CJ = (tx0 >> 1) + 2 * cq;
+    const int I = 2 * CI, J = 2 * CJ;
+    const bool valid = CI < gc.H && CJ < gc.W;
+    const bool fast = valid && I >= 1 && I + 1 <= g.H - 3 && J >= 1 && J + 3 <= g.W - 3;
+    if (__all_sync(0xffffffffu, fast || !valid)) {
+      if (!valid) continue;
+      const int y = I - ry0, m = (J - rx0) >> 1;  // m even: 8-byte aligned pairs
+      const float *E = U + y * G::S + 4 + m, *O = E + G::PLANE;
+      const float *FE = F + y * G::S + 4 + m, *FO = FE + G::PLANE;
+      float2 e[4], o[4];  // rows y-1 .. y+2, cells m, m+1 of each plane
 #pragma unroll
-    for (int j = 0; j < G::TX / 2 / kBX; ++j) {
-      const int CI = (ty0 >> 1) + threadIdx.y + kBY * i;
-      const int CJ = (tx0 >> 1) + threadIdx.x + kBX * j;
-      if (CI >= gc.H || CJ >= gc.W) continue;
-      float sum = 0.f;
+      for (int r = 0; r < 4; ++r) {
+        e[r] = *reinterpret_cast<const float2 *>(E + (r - 1) * G::S);
+        o[r] = *reinterpret_cast<const float2 *>(O + (r - 1) * G::S);
+      }
+      float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int di = 0; di < 2; ++di)
+      for (int kk = 0; kk < 2; ++kk) {
+        const int r = kk + 1;
+        const float oL = O[kk * G::S - 1], eR = E[kk * G::S + 2];
+        const float2 fe = *reinterpret_cast<const float2 *>(FE + kk * G::S);
+        const float2 fo = *reinterpret_cast<const float2 *>(FO + kk * G::S);
+        float u = e[r].x;
+        s0 += fe.x - (((o[r].x - u) + (oL - u)) + ((e[r + 1].x - u) + (e[r - 1].x - u)));
+        u = o[r].x;
+        s0 += fo.x - (((e[r].y - u) + (e[r].x - u)) + ((o[r + 1].x - u) + (o[r - 1].x - u)));
+        u = e[r].y;
+        s1 += fe.y - (((o[r].y - u) + (o[r].x - u)) + ((e[r + 1].y - u) + (e[r - 1].y - u)));
+        u = o[r].y;
+        s1 += fo.y - (((eR - u) + (e[r].y - u)) + ((o[r + 1].y - u) + (o[r - 1].y - u)));
+      }
+      fc[(size_t)CI * gc.W + CJ] = s0;
+      fc[(size_t)CI * gc.W + CJ + 1] = s1;
+    } else if (valid) {
 #pragma unroll
-        for (int dj = 0; dj < 2; ++dj) {
-          const int gy = 2 * CI + di, gx = 2 * CJ + dj;
-          if (gy < g.H && gx < g.W) sum += tile_residual<G>(U, F, g, gy - ry0, gx - rx0, gy, gx);
-        }
-      fc[(size_t)CI * gc.W + CJ] = sum;
+      for (int d = 0; d < 2; ++d) {
+        const int cj = CJ + d;
+        if (cj >= gc.W) break;
+        float sum = 0.f;
+#pragma unroll
+        for (int di = 0; di < 2; ++di)
+#pragma unroll
+          for (int dj = 0; dj < 2; ++dj) {
+            const int gy = I + di, gx = 2 * cj + dj;
+            if (gy < g.H && gx < g.W) sum += tile_residual<G>(U, F, g, gy - ry0, gx - rx0, gy, gx);
+          }
+        fc[(size_t)CI * gc.W + cj] = sum;
+      }
     }
+  }
 }
 
 // Coarse values around the region: rows cy0.., columns cx0.. of the coarse level.
@@ -470,6 +588,80 @@ __device__ __forceinline__ void prolong_tile(float *U, const float *EC, const Le
   }
 }
 
+// Finest level, W % 4 == 0: u_{k+1} = u_k + e in float-float, r_{k+1} = r_k - L e
+// (r_k is F, e is U), the sums of u_{k+1} and of r_{k+1}^2; 16-byte global
+// accesses, residuals from the split planes away from the border (warp-uniform).
+template <class G>
+__device__ __forceinline__ void finest_epilogue4(const float *U, const float *F, const LevelGeom &g,
+                                                 int ty0, int tx0, int k, float *uh, float *ul,
+                                                 float *rn, Ctrl *ctrl, int c) {
+  constexpr int NG = G::TX / 4, TOT = G::TY * NG, PER = TOT / kMgThreads;
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  float4 vh[PER], vl[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * kMgThreads;
+    const int y = idx / NG, q = idx - y * NG;
+    const int gy = ty0 + y, gx = tx0 + 4 * q;
+    const bool in = k > 0 && gy < g.H && gx < g.W;
+    const size_t p = (size_t)gy * g.W + gx;
+    vh[i] = in ? *reinterpret_cast<const float4 *>(uh + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    vl[i] = in ? *reinterpret_cast<const float4 *>(ul + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float su = 0.f, rn2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * kMgThreads;
+    const int y = idx / NG, q = idx - y * NG;
+    const int gy = ty0 + y, gx = tx0 + 4 * q;
+    const bool valid = gy < g.H && gx < g.W;
+    const int yy = y + G::HY, xx = 4 * q + G::HX, m = xx >> 1;
+    const float *E = U + yy * G::S + 4 + m, *O = E + G::PLANE;
+    const float2 e = *reinterpret_cast<const float2 *>(E);
+    const float2 o = *reinterpret_cast<const float2 *>(O);
+    float r[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool fast = valid && gy >= 1 && gy <= g.H - 3 && gx >= 1 && gx + 3 <= g.W - 3;
+    if (__all_sync(0xffffffffu, fast || !valid)) {
+      if (valid) {
+        const float oL = O[-1], eR = E[2];
+        const float2 eN = *reinterpret_cast<const float2 *>(E - G::S);
+        const float2 eS = *reinterpret_cast<const float2 *>(E + G::S);
+        const float2 oN = *reinterpret_cast<const float2 *>(O - G::S);
+        const float2 oS = *reinterpret_cast<const float2 *>(O + G::S);
+        const float *FE = F + yy * G::S + 4 + m;
+        const float2 fe = *reinterpret_cast<const float2 *>(FE);
+        const float2 fo = *reinterpret_cast<const float2 *>(FE + G::PLANE);
+        r[0] = fe.x - (((o.x - e.x) + (oL - e.x)) + ((eS.x - e.x) + (eN.x - e.x)));
+        r[1] = fo.x - (((e.y - o.x) + (e.x - o.x)) + ((oS.x - o.x) + (oN.x - o.x)));
+        r[2] = fe.y - (((o.y - e.y) + (o.x - e.y)) + ((eS.y - e.y) + (eN.y - e.y)));
+        r[3] = fo.y - (((eR - o.y) + (e.y - o.y)) + ((oS.y - o.y) + (oN.y - o.y)));
+      }
+    } else if (valid) {
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        r[d] = tile_residual<G>(const_cast<float *>(U), const_cast<float *>(F), g, yy, xx + d, gy,
+                                gx + d);
+    }
+    if (!valid) continue;
+    const float ev[4] = {e.x, o.x, e.y, o.y};
+    float hv[4] = {vh[i].x, vh[i].y, vh[i].z, vh[i].w}, lv[4] = {vl[i].x, vl[i].y, vl[i].z, vl[i].w};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      ds_add(hv[d], lv[d], ev[d]);
+      su += hv[d] + lv[d];
+      rn2 = fmaf(r[d], r[d], rn2);
+    }
+    const size_t p = (size_t)gy * g.W + gx;
+    *reinterpret_cast<float4 *>(uh + p) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4 *>(ul + p) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    *reinterpret_cast<float4 *>(rn + p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+  su = block_sum(su);
+  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+  rn2 = block_sum(rn2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+}
+
 // ------------------------------------------------------------------ level kernels
 
 struct LvArgs {
@@ -509,7 +701,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
-  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
+  load_tile<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
   zero_split<G>(U);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
@@ -518,12 +710,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
     half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1, a.omega);
     __syncthreads();
   }
-  float *uo = a.u + (size_t)c * g.plane;
-  for (int y = threadIdx.y; y < G::TY; y += kBY)
-    for (int x = threadIdx.x; x < G::TX; x += kBX) {
-      const int gy = ty0 + y, gx = tx0 + x;
-      if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = at<G>(U, y + G::HY, x + G::HX);
-    }
+  store_tile<G>(U, a.u + (size_t)c * g.plane, g, ty0, tx0);
   restrict_tile<G>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
 }
 
@@ -542,8 +729,8 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
   const int cy0 = (ry0 >> 1) - 1, cx0 = (rx0 >> 1) - 1;
-  load_split<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
-  load_split<G>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
+  load_tile<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
+  load_tile<G>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
   load_coarse<G>(EC, a.uc + (size_t)c * a.gc.plane, a.gc, cy0, cx0);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
@@ -555,16 +742,15 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
     __syncthreads();
   }
   if (!a.level0) {
-    float *uo = a.u + (size_t)c * g.plane;
-    for (int y = threadIdx.y; y < G::TY; y += kBY)
-      for (int x = threadIdx.x; x < G::TX; x += kBX) {
-        const int gy = ty0 + y, gx = tx0 + x;
-        if (gy < g.H && gx < g.W) uo[(size_t)gy * g.W + gx] = at<G>(U, y + G::HY, x + G::HX);
-      }
+    store_tile<G>(U, a.u + (size_t)c * g.plane, g, ty0, tx0);
     return;
   }
   const size_t cb = (size_t)c * g.plane;
   float *uh = a.uhi + cb, *ul = a.ulo + cb, *rn = a.rb[k & 1] + cb;
+  if (vec4_ok(g)) {
+    finest_epilogue4<G>(U, F, g, ty0, tx0, k, uh, ul, rn, ctrl, c);
+    return;
+  }
   constexpr int NY = G::TY / kBY, NX = G::TX / kBX;
   float vh[NY][NX], vl[NY][NX];
 #pragma unroll
