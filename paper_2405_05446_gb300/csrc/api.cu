@@ -121,6 +121,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
     const size_t b = sizeof(float) * (size_t)C * p->lv[l].plane;
     p->off_lu[l] = cv.take(b);
     p->off_lf[l] = cv.take(b);
+    p->off_luo[l] = cv.take(b);
   }
   p->total = cv.cur;
   return true;

@@ -88,7 +88,8 @@ struct Plan {
   size_t off_range, off_active, off_mask;              // per tile
   size_t off_maps;                                     // [C][2][H][W]
   size_t off_rho, off_uhi, off_ulo, off_e0, off_r[2];  // level 0 [C][H][W]
-  size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1
+  size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1: down-pass u, f
+  size_t off_luo[kMaxLevels];                          // levels >= 1: up-pass u (never in place)
   size_t off_coarse;                                   // tag + FP64 inverse
   int levels;         // number of levels (finest = 0, coarsest = levels-1)
   int nc;             // unknowns on the coarsest level

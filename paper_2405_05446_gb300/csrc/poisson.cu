@@ -36,7 +36,9 @@
 // that path, the few at the border a scalar path with the exact boundary
 // coefficients. Down kernels fuse the pre-sweeps with residual and restriction,
 // up kernels the prolongation with the post-sweeps (and, on the finest level,
-// the update of u, the new residual and its norm). Levels under kSmallLevel
+// the update of u, the new residual and its norm). An up pass writes its level
+// to an array of its own: the CTAs of one launch read each other's tiles as
+// halo, so an in-place update would race. Levels under kSmallLevel
 // cells use 16 x 64 tiles. The levels from the first with at most kTailCells
 // cells per channel down to the coarsest run in one kernel, one CTA per
 // channel, entirely in shared memory; it also solves the coarsest grid with
@@ -667,7 +669,9 @@ __device__ __forceinline__ void finest_epilogue4(const float *U, const float *F,
 struct LvArgs {
   LevelGeom g, gc;
   const float *f;    // right-hand side (level >= 1)
-  float *u;          // correction of this level
+  float *u;          // correction of this level after the down pass
+  float *uo;         // correction after the up pass (levels >= 1): a separate array, because
+                     // an up CTA reads its halo from u while its neighbours write their tiles
   float *fc;         // coarse right-hand side (down)
   const float *uc;   // coarse correction (up)
   int level0;        // finest level: right-hand side r_k, u update
@@ -742,7 +746,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
     __syncthreads();
   }
   if (!a.level0) {
-    store_tile<G>(U, a.u + (size_t)c * g.plane, g, ty0, tx0);
+    store_tile<G>(U, a.uo + (size_t)c * g.plane, g, ty0, tx0);
     return;
   }
   const size_t cb = (size_t)c * g.plane;
@@ -1436,8 +1440,9 @@ struct Cycle {
     a.gc = p->lv[l + 1];
     a.f = l > 0 ? (const float *)(ws + p->off_lf[l]) : nullptr;
     a.u = (float *)(ws + (l > 0 ? p->off_lu[l] : p->off_e0));
+    a.uo = l > 0 ? (float *)(ws + p->off_luo[l]) : nullptr;
     a.fc = (float *)(ws + p->off_lf[l + 1]);
-    a.uc = (const float *)(ws + p->off_lu[l + 1]);
+    a.uc = (const float *)(ws + p->off_luo[l + 1]);
     a.level0 = l == 0;
     a.rho = (const float *)(ws + p->off_rho);
     a.rb[0] = (float *)(ws + p->off_r[0]);
@@ -1457,7 +1462,7 @@ struct Cycle {
     for (int i = 0; i < a.n; ++i) a.lv[i] = p->lv[t + i];
     tail_layout(a.lv, a.n, &a);
     a.f_top = (const float *)(ws + p->off_lf[t]);
-    a.u_top = (float *)(ws + p->off_lu[t]);
+    a.u_top = (float *)(ws + p->off_luo[t]);
     a.Minv = Minv;
     a.nu1 = nu1;
     a.nu2 = nu2;

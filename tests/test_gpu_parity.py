@@ -181,6 +181,23 @@ def test_poisson_recovers_known_image_1080p():
     assert img_err(img, ref)[1] <= IMG_TOL
 
 
+@pytest.mark.parametrize("max_cycles", [1, 30])
+def test_identical_channels_give_identical_images_1080p(max_cycles):
+    """Channels are independent problems: four copies of one field at 1080p (enough
+    CTAs for several waves per level) must come out bit-identical. A kernel that
+    reads cells another CTA of the same launch rewrites (an in-place level update)
+    breaks this, even where the solve still converges."""
+    rng = np.random.default_rng(5)
+    H, W, C = 1080, 1920, 4
+    one = rng.laplace(0, 0.1, (1, 2, H, W)).astype(np.float32)
+    maps = np.repeat(one, C, axis=0)
+    img, st = gpu_poisson(maps, [0.5] * C, G.solver_opts(max_cycles=max_cycles, rtol=0.0 if max_cycles == 1 else 1e-6))
+    for c in range(1, C):
+        assert np.array_equal(img[c], img[0]), c
+    if max_cycles > 1:
+        assert st["status"] == 0 and st["cycles"] <= 5, st
+
+
 def test_poisson_zero_field_gives_mean():
     img, st = gpu_poisson(np.zeros((2, 2, 40, 50), np.float32), [0.25, 0.75])
     assert st["status"] == 0 and st["cycles"] == 0
