@@ -34,6 +34,9 @@ WORKLOADS = {
     "lap1080p": "the prims1080p Gaussians carrying one Laplacian value per channel (Eq. gdgs, "
                 "Laplace(0,0.05)) instead of a gradient: composite = rho, no divergence",
 }
+# Pair-buffer capacity per workload: at 4K a Gaussian covers 4x the tiles it covers
+# at 1080p (21.9M pairs for 1M Gaussians).
+PAIRS_PER_GAUSSIAN = {"prims4k": 32}
 METRIC = "1080p views/s (splat+Poisson, FP32 path, rel. residual <= 1e-6)"
 HBM_FALLBACK_GBS = 6800.0
 
@@ -208,6 +211,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-views", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="number format of the multigrid corrections and coarse right-hand sides")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -236,8 +241,10 @@ def main():
 
     scene, cam, mean, rtol = make_workload(args.workload)
     C, H, W = scene.channels, cam.height, cam.width
-    sopts = G.solver_opts(rtol=rtol)
-    r = G.Renderer(scene.n, C, W, H, sopts=sopts, device=dev)
+    storage = {"f32": 0, "bf16": 1, "f16": 2}[args.storage]
+    sopts = G.solver_opts(rtol=rtol, storage=storage)
+    ropts = G.raster_opts(pairs_per_gaussian=PAIRS_PER_GAUSSIAN.get(args.workload, 16))
+    r = G.Renderer(scene.n, C, W, H, ropts=ropts, sopts=sopts, device=dev)
     g = G.gaussians_to_device(scene, dev)
     out = torch.empty((C, H, W), device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -312,11 +319,11 @@ def main():
     # per-kernel CUDA-event times (outside the timed region). Profiling launches
     # the cycle loop directly; max_cycles = the observed count keeps it free of
     # launches after convergence, so it does the same work as the graph.
-    sopts_prof = G.solver_opts(rtol=rtol, max_cycles=max(1, st["cycles"]))
+    sopts_prof = G.solver_opts(rtol=rtol, max_cycles=max(1, st["cycles"]), storage=storage)
     G.profile_begin()
     for _ in range(args.profile_views):
         flush.zero_()
-        G.render_view(g, cam, mean, out, r.ws, r.ropts, sopts_prof)
+        G.render_view(g, cam, mean, out, r.ws, ropts, sopts_prof)
     torch.cuda.synchronize()
     prof = G.profile_end()
 
@@ -362,7 +369,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                        "solver": {"nu1": sopts.nu1, "nu2": sopts.nu2, "omega": round(sopts.omega, 4),
-                                  "coarse_max_dim": sopts.coarse_max_dim, "rtol": rtol},
+                                  "coarse_max_dim": sopts.coarse_max_dim, "rtol": rtol,
+                                  "storage": args.storage},
                        "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed views (256 MB write)"},
             "mpix_per_s": value * W * H / 1e6,

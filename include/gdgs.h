@@ -133,7 +133,13 @@ typedef struct gdgs_raster_opts {
  *                   (Eq. thresh); 0 keeps rho as it is                 (0)
  *   omega           over-relaxation of the red-black Gauss-Seidel smoother,
  *                   u <- u + omega (u_GS - u), in [0.5, 1.9]; it changes how
- *                   fast the cycles converge, not what they converge to (1.2) */
+ *                   fast the cycles converge, not what they converge to (1.2)
+ *   storage         number format of the multigrid corrections and coarse
+ *                   right-hand sides in memory: GDGS_STORAGE_F32, _BF16 or
+ *                   _F16 (arithmetic is FP32 throughout; the residual r_k,
+ *                   the iterate (float-float) and the coarse solve (FP64)
+ *                   keep their precision, so the cycles are an iterative
+ *                   refinement that reaches rtol in every format)  (F32) */
 typedef struct gdgs_solver_opts {
   int32_t nu1;
   int32_t nu2;
@@ -142,7 +148,10 @@ typedef struct gdgs_solver_opts {
   int32_t coarse_max_dim;
   float rho_threshold;
   float omega;
+  int32_t storage;
 } gdgs_solver_opts;
+
+enum { GDGS_STORAGE_F32 = 0, GDGS_STORAGE_BF16 = 1, GDGS_STORAGE_F16 = 2 };
 
 /* Filled by gdgs_sync_status() from the workspace after the stream has drained. */
 typedef struct gdgs_solve_stats {

@@ -30,6 +30,7 @@ _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
 
 
+STORAGE_F32, STORAGE_BF16, STORAGE_F16 = 0, 1, 2
 ATTR_GRADIENT = 0
 ATTR_LAPLACIAN = 1
 
@@ -51,7 +52,8 @@ class RasterOpts(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("nu1", _i32), ("nu2", _i32), ("max_cycles", _i32), ("rtol", _f),
-                ("coarse_max_dim", _i32), ("rho_threshold", _f), ("omega", _f)]
+                ("coarse_max_dim", _i32), ("rho_threshold", _f), ("omega", _f),
+                ("storage", _i32)]
 
 
 class SolveStats(ctypes.Structure):

@@ -50,7 +50,8 @@ bool solver_opts_ok(const gdgs_solver_opts &o) {
   return o.nu1 >= 1 && o.nu1 <= 3 && o.nu2 >= 1 && o.nu2 <= 3 && o.max_cycles >= 1 &&
          o.max_cycles <= kMaxCycles && isfinite(o.rtol) && o.rtol >= 0.f &&
          o.coarse_max_dim >= 2 && o.coarse_max_dim <= 16 && isfinite(o.rho_threshold) &&
-         o.rho_threshold >= 0.f && o.omega >= 0.5f && o.omega <= 1.9f;
+         o.rho_threshold >= 0.f && o.omega >= 0.5f && o.omega <= 1.9f && o.storage >= 0 &&
+         o.storage <= 2;
 }
 
 }  // namespace
@@ -316,6 +317,7 @@ void gdgs_default_solver_opts(gdgs_solver_opts *o) {
   o->coarse_max_dim = 8;
   o->rho_threshold = 0.f;
   o->omega = 1.2f;
+  o->storage = GDGS_STORAGE_F32;
 }
 
 const char *gdgs_status_string(int s) {
@@ -416,6 +418,7 @@ static int poisson_common(const float *field, int input_is_rho, const uint8_t *t
   a.nu1 = so.nu1;
   a.nu2 = so.nu2;
   a.omega = so.omega;
+  a.storage = so.storage;
   a.max_cycles = so.max_cycles;
   a.rtol = so.rtol;
   a.plan = &p;
@@ -474,6 +477,7 @@ int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const floa
   a.nu1 = so.nu1;
   a.nu2 = so.nu2;
   a.omega = so.omega;
+  a.storage = so.storage;
   a.max_cycles = so.max_cycles;
   a.rtol = so.rtol;
   a.plan = &p;

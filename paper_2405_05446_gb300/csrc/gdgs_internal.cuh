@@ -41,6 +41,7 @@ struct Ctrl {
   double rho_sum[GDGS_MAX_CHANNELS];         // sum and sum of squares of rho per channel
   double rho_sq[GDGS_MAX_CHANNELS];
   float rho_mean[GDGS_MAX_CHANNELS];         // the constant removed from rho (least squares)
+  float escale[kMaxCycles + 1];              // cycle k solves for s_k e (a power of two)
 };
 
 // Diagnostics hooks around every kernel launch (diag.cu).
@@ -184,6 +185,7 @@ struct PoissonArgs {
   int nu1, nu2, max_cycles;
   float rtol;
   float omega;              // smoother over-relaxation
+  int storage;              // GDGS_STORAGE_*: multigrid corrections and coarse right-hand sides
   const Plan *plan;
   char *ws;
   Ctrl *ctrl;

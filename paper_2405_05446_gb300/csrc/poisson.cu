@@ -53,6 +53,9 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -65,6 +68,64 @@ constexpr int kMgThreads = kBX * kBY;
 // with fewer cells per channel than kSmallLevel 16 x 64 (more CTAs, shorter
 // serial work per CTA, which is what bounds the small grids).
 constexpr long long kSmallLevel = 160000;
+
+// ------------------------------------------------------------------ storage formats
+//
+// Multigrid corrections and coarse right-hand sides live in memory as FP32,
+// BF16 or FP16 (GDGS_STORAGE_*); all arithmetic is FP32. The format is a kernel
+// argument, so the branches below are uniform.
+
+__device__ __forceinline__ const void *s_at(const void *p, size_t n, int s) {
+  return reinterpret_cast<const char *>(p) + n * (s == GDGS_STORAGE_F32 ? 4 : 2);
+}
+__device__ __forceinline__ void *s_at(void *p, size_t n, int s) {
+  return reinterpret_cast<char *>(p) + n * (s == GDGS_STORAGE_F32 ? 4 : 2);
+}
+
+__device__ __forceinline__ float s_ld(const void *p, size_t i, int s) {
+  if (s == GDGS_STORAGE_BF16) return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p) + i));
+  if (s == GDGS_STORAGE_F16) return __half2float(__ldg(reinterpret_cast<const __half *>(p) + i));
+  return __ldg(reinterpret_cast<const float *>(p) + i);
+}
+
+__device__ __forceinline__ void s_st(void *p, size_t i, float v, int s) {
+  if (s == GDGS_STORAGE_BF16) reinterpret_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(v);
+  else if (s == GDGS_STORAGE_F16) reinterpret_cast<__half *>(p)[i] = __float2half_rn(v);
+  else reinterpret_cast<float *>(p)[i] = v;
+}
+
+// Four consecutive elements starting at i (i % 4 == 0, 16- or 8-byte aligned).
+__device__ __forceinline__ float4 s_ld4(const void *p, size_t i, int s) {
+  if (s == GDGS_STORAGE_F32) return __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(p) + i));
+  const uint2 r = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const unsigned short *>(p) + i));
+  float2 a, b;
+  if (s == GDGS_STORAGE_BF16) {
+    a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+    b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+  } else {
+    a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+    b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+  }
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ void s_st4(void *p, size_t i, float4 v, int s) {
+  if (s == GDGS_STORAGE_F32) {
+    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(p) + i) = v;
+    return;
+  }
+  uint2 r;
+  if (s == GDGS_STORAGE_BF16) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    r.x = *reinterpret_cast<const unsigned *>(&a);
+    r.y = *reinterpret_cast<const unsigned *>(&b);
+  } else {
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    r.x = *reinterpret_cast<const unsigned *>(&a);
+    r.y = *reinterpret_cast<const unsigned *>(&b);
+  }
+  *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(p) + i) = r;
+}
 
 // ------------------------------------------------------------------ operator
 
@@ -222,8 +283,9 @@ __device__ __forceinline__ void zero_pads(float *A) {
 // Loads src (a level array) into the split layout; cells outside the grid read 0.
 // All loads of a thread are issued before its stores, so they overlap.
 template <class G>
-__device__ __forceinline__ void load_split(float *A, const float *__restrict__ src,
-                                           const LevelGeom &g, int ry0, int rx0, float off = 0.f) {
+__device__ __forceinline__ void load_split(float *A, const void *__restrict__ src, int sf,
+                                           const LevelGeom &g, int ry0, int rx0, float off,
+                                           float scale) {
   constexpr int NY = (G::RY + kBY - 1) / kBY, NX = (G::RXP + kBX - 1) / kBX;
   float v[NY][NX];
 #pragma unroll
@@ -233,7 +295,9 @@ __device__ __forceinline__ void load_split(float *A, const float *__restrict__ s
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       const int x = threadIdx.x + kBX * j, gx = rx0 + x;
-      v[i][j] = (rin && x < G::RXP && gx >= 0 && gx < g.W) ? __ldg(src + (size_t)gy * g.W + gx) - off : 0.f;
+      v[i][j] = (rin && x < G::RXP && gx >= 0 && gx < g.W)
+                    ? (s_ld(src, (size_t)gy * g.W + gx, sf) - off) * scale
+                    : 0.f;
     }
   }
 #pragma unroll
@@ -250,8 +314,9 @@ __device__ __forceinline__ void load_split(float *A, const float *__restrict__ s
 // every group of 4 cells is wholly inside or outside the grid. A group (x, x+1,
 // x+2, x+3) goes to the even plane as (x, x+2) and to the odd one as (x+1, x+3).
 template <class G>
-__device__ __forceinline__ void load_split4(float *A, const float *__restrict__ src,
-                                            const LevelGeom &g, int ry0, int rx0, float off) {
+__device__ __forceinline__ void load_split4(float *A, const void *__restrict__ src, int sf,
+                                            const LevelGeom &g, int ry0, int rx0, float off,
+                                            float scale) {
   constexpr int NG = G::RXP / 4, TOT = G::RY * NG;
   constexpr int PER = (TOT + kMgThreads - 1) / kMgThreads;
   const int tid = threadIdx.y * kBX + threadIdx.x;
@@ -262,8 +327,7 @@ __device__ __forceinline__ void load_split4(float *A, const float *__restrict__ 
     const int y = idx / NG, q = idx - y * NG;
     const int gy = ry0 + y, gx = rx0 + 4 * q;
     const bool in = idx < TOT && gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-    v[i] = in ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)gy * g.W + gx))
-              : make_float4(off, off, off, off);
+    v[i] = in ? s_ld4(src, (size_t)gy * g.W + gx, sf) : make_float4(off, off, off, off);
   }
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
@@ -271,8 +335,9 @@ __device__ __forceinline__ void load_split4(float *A, const float *__restrict__ 
     if (idx < TOT) {
       const int y = idx / NG, q = idx - y * NG;
       float *row = A + y * G::S + 4 + 2 * q;
-      *reinterpret_cast<float2 *>(row) = make_float2(v[i].x - off, v[i].z - off);
-      *reinterpret_cast<float2 *>(row + G::PLANE) = make_float2(v[i].y - off, v[i].w - off);
+      *reinterpret_cast<float2 *>(row) = make_float2((v[i].x - off) * scale, (v[i].z - off) * scale);
+      *reinterpret_cast<float2 *>(row + G::PLANE) =
+          make_float2((v[i].y - off) * scale, (v[i].w - off) * scale);
     }
   }
   zero_pads<G>(A);
@@ -282,17 +347,19 @@ __device__ __forceinline__ void load_split4(float *A, const float *__restrict__ 
 // are then 16-byte multiples as well; level arrays are 256-byte aligned).
 __device__ __forceinline__ bool vec4_ok(const LevelGeom &g) { return (g.W & 3) == 0; }
 
+// (src - off) * scale for cells inside the grid, 0 outside.
 template <class G>
-__device__ __forceinline__ void load_tile(float *A, const float *__restrict__ src,
-                                          const LevelGeom &g, int ry0, int rx0, float off = 0.f) {
-  if (vec4_ok(g)) load_split4<G>(A, src, g, ry0, rx0, off);
-  else load_split<G>(A, src, g, ry0, rx0, off);
+__device__ __forceinline__ void load_tile(float *A, const void *__restrict__ src, int sf,
+                                          const LevelGeom &g, int ry0, int rx0, float off,
+                                          float scale) {
+  if (vec4_ok(g)) load_split4<G>(A, src, sf, g, ry0, rx0, off, scale);
+  else load_split<G>(A, src, sf, g, ry0, rx0, off, scale);
 }
 
 // Writes the output tile (region rows HY.., columns HX..) of U to dst.
 template <class G>
-__device__ __forceinline__ void store_tile(const float *U, float *dst, const LevelGeom &g, int ty0,
-                                           int tx0) {
+__device__ __forceinline__ void store_tile(const float *U, void *dst, int sf, const LevelGeom &g,
+                                           int ty0, int tx0) {
   const int tid = threadIdx.y * kBX + threadIdx.x;
   if (vec4_ok(g)) {
     constexpr int NG = G::TX / 4, TOT = G::TY * NG;
@@ -305,14 +372,15 @@ __device__ __forceinline__ void store_tile(const float *U, float *dst, const Lev
       const float *row = U + (y + G::HY) * G::S + 4 + ((4 * q + G::HX) >> 1);
       const float2 e = *reinterpret_cast<const float2 *>(row);
       const float2 o = *reinterpret_cast<const float2 *>(row + G::PLANE);
-      *reinterpret_cast<float4 *>(dst + (size_t)gy * g.W + gx) = make_float4(e.x, o.x, e.y, o.y);
+      s_st4(dst, (size_t)gy * g.W + gx, make_float4(e.x, o.x, e.y, o.y), sf);
     }
     return;
   }
   for (int y = threadIdx.y; y < G::TY; y += kBY)
     for (int x = threadIdx.x; x < G::TX; x += kBX) {
       const int gy = ty0 + y, gx = tx0 + x;
-      if (gy < g.H && gx < g.W) dst[(size_t)gy * g.W + gx] = at<G>(const_cast<float *>(U), y + G::HY, x + G::HX);
+      if (gy < g.H && gx < g.W)
+        s_st(dst, (size_t)gy * g.W + gx, at<G>(const_cast<float *>(U), y + G::HY, x + G::HX), sf);
     }
 }
 
@@ -445,7 +513,8 @@ __device__ __forceinline__ float tile_residual(float *U, float *F, const LevelGe
 // general cell formula.
 template <class G>
 __device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeom &g,
-                                              const LevelGeom &gc, int ty0, int tx0, float *fc) {
+                                              const LevelGeom &gc, int ty0, int tx0, void *fc,
+                                              int sf, float fout) {
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
   const int tid = threadIdx.y * kBX + threadIdx.x;
   constexpr int CW2 = G::TX / 4, NP = (G::TY / 2) * CW2;
@@ -486,8 +555,8 @@ __device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeo
         u = o[r].y;
         s1 += fo.y - (((eR - u) + (e[r].y - u)) + ((o[r + 1].y - u) + (o[r - 1].y - u)));
       }
-      fc[(size_t)CI * gc.W + CJ] = s0;
-      fc[(size_t)CI * gc.W + CJ + 1] = s1;
+      s_st(fc, (size_t)CI * gc.W + CJ, s0 * fout, sf);
+      s_st(fc, (size_t)CI * gc.W + CJ + 1, s1 * fout, sf);
     } else if (valid) {
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
@@ -501,7 +570,7 @@ __device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeo
             const int gy = I + di, gx = 2 * cj + dj;
             if (gy < g.H && gx < g.W) sum += tile_residual<G>(U, F, g, gy - ry0, gx - rx0, gy, gx);
           }
-        fc[(size_t)CI * gc.W + cj] = sum;
+        s_st(fc, (size_t)CI * gc.W + cj, sum * fout, sf);
       }
     }
   }
@@ -509,7 +578,7 @@ __device__ __forceinline__ void restrict_tile(float *U, float *F, const LevelGeo
 
 // Coarse values around the region: rows cy0.., columns cx0.. of the coarse level.
 template <class G>
-__device__ __forceinline__ void load_coarse(float *EC, const float *__restrict__ uc,
+__device__ __forceinline__ void load_coarse(float *EC, const void *__restrict__ uc, int sf,
                                             const LevelGeom &gc, int cy0, int cx0) {
   constexpr int NY = (G::CRY + kBY - 1) / kBY, NX = (G::CRX + kBX - 1) / kBX;
   float v[NY][NX];
@@ -520,7 +589,7 @@ __device__ __forceinline__ void load_coarse(float *EC, const float *__restrict__
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       const int x = threadIdx.x + kBX * j, gx = cx0 + x;
-      v[i][j] = (rin && x < G::CRX && gx >= 0 && gx < gc.W) ? __ldg(uc + (size_t)gy * gc.W + gx) : 0.f;
+      v[i][j] = (rin && x < G::CRX && gx >= 0 && gx < gc.W) ? s_ld(uc, (size_t)gy * gc.W + gx, sf) : 0.f;
     }
   }
 #pragma unroll
@@ -596,7 +665,7 @@ __device__ __forceinline__ void prolong_tile(float *U, const float *EC, const Le
 template <class G>
 __device__ __forceinline__ void finest_epilogue4(const float *U, const float *F, const LevelGeom &g,
                                                  int ty0, int tx0, int k, float *uh, float *ul,
-                                                 float *rn, Ctrl *ctrl, int c) {
+                                                 float *rn, Ctrl *ctrl, int c, float inv_s) {
   constexpr int NG = G::TX / 4, TOT = G::TY * NG, PER = TOT / kMgThreads;
   const int tid = threadIdx.y * kBX + threadIdx.x;
   float4 vh[PER], vl[PER];
@@ -645,7 +714,9 @@ __device__ __forceinline__ void finest_epilogue4(const float *U, const float *F,
                                 gx + d);
     }
     if (!valid) continue;
-    const float ev[4] = {e.x, o.x, e.y, o.y};
+    const float ev[4] = {e.x * inv_s, o.x * inv_s, e.y * inv_s, o.y * inv_s};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) r[d] *= inv_s;
     float hv[4] = {vh[i].x, vh[i].y, vh[i].z, vh[i].w}, lv[4] = {vl[i].x, vl[i].y, vl[i].z, vl[i].w};
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
@@ -666,14 +737,21 @@ __device__ __forceinline__ void finest_epilogue4(const float *U, const float *F,
 
 // ------------------------------------------------------------------ level kernels
 
+// Arrays of a level in the storage format sf (corrections, coarse right-hand
+// sides) and in FP32 (the finest level's r_k and iterate). Cycle k solves for
+// s_k e, s_k = ctrl->escale[k] a power of two that brings the RMS of r_k near 1;
+// a level l >= 1 stores its right-hand side times 4^-l. Both scalings are exact,
+// and they keep FP16 values in range.
 struct LvArgs {
   LevelGeom g, gc;
-  const float *f;    // right-hand side (level >= 1)
-  float *u;          // correction of this level after the down pass
-  float *uo;         // correction after the up pass (levels >= 1): a separate array, because
+  const void *f;     // right-hand side times 4^-l (level >= 1)
+  void *u;           // correction of this level after the down pass
+  void *uo;          // correction after the up pass (levels >= 1): a separate array, because
                      // an up CTA reads its halo from u while its neighbours write their tiles
-  float *fc;         // coarse right-hand side (down)
-  const float *uc;   // coarse correction (up)
+  void *fc;          // coarse right-hand side times 4^-(l+1) (down)
+  const void *uc;    // coarse correction (up)
+  int sf;            // GDGS_STORAGE_* of f, u, uo, fc, uc
+  float fin, fout;   // 4^l and 4^-(l+1)
   int level0;        // finest level: right-hand side r_k, u update
   const float *rho;  // r_0
   float *rb[2];      // r_{k+1} is written to rb[k & 1]
@@ -681,15 +759,29 @@ struct LvArgs {
   float omega;       // smoother over-relaxation
 };
 
-__device__ __forceinline__ const float *rhs_of(const LvArgs &a, int k) {
-  if (!a.level0) return a.f;
-  return k == 0 ? a.rho : a.rb[(k - 1) & 1];
-}
-
+// Right-hand side of this level for channel c in cycle k: (src - off) * scale.
 // r_0 = rho - mean(rho): a field whose sum is not zero (possible for the
 // composite of Laplacian values) is solved in the least-squares sense.
-__device__ __forceinline__ float rhs_offset(const LvArgs &a, const Ctrl *ctrl, int k, int c) {
-  return (a.level0 && k == 0) ? ctrl->rho_mean[c] : 0.f;
+struct Rhs {
+  const void *src;
+  int sf;
+  float off, scale;
+};
+
+__device__ __forceinline__ Rhs rhs_of(const LvArgs &a, const Ctrl *ctrl, int k, int c) {
+  Rhs r;
+  if (!a.level0) {
+    r.src = s_at(a.f, (size_t)c * a.g.plane, a.sf);
+    r.sf = a.sf;
+    r.off = 0.f;
+    r.scale = a.fin;
+    return r;
+  }
+  r.src = (k == 0 ? a.rho : a.rb[(k - 1) & 1]) + (size_t)c * a.g.plane;
+  r.sf = GDGS_STORAGE_F32;
+  r.off = k == 0 ? ctrl->rho_mean[c] : 0.f;
+  r.scale = ctrl->escale[k];
+  return r;
 }
 
 // Down: nu1 sweeps on L u = f from u = 0, write u, restrict f - L u.
@@ -705,7 +797,8 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
-  load_tile<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
+  const Rhs rh = rhs_of(a, ctrl, k, c);
+  load_tile<G>(F, rh.src, rh.sf, g, ry0, rx0, rh.off, rh.scale);
   zero_split<G>(U);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
@@ -714,8 +807,8 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
     half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1, a.omega);
     __syncthreads();
   }
-  store_tile<G>(U, a.u + (size_t)c * g.plane, g, ty0, tx0);
-  restrict_tile<G>(U, F, g, a.gc, ty0, tx0, a.fc + (size_t)c * a.gc.plane);
+  store_tile<G>(U, s_at(a.u, (size_t)c * g.plane, a.sf), a.sf, g, ty0, tx0);
+  restrict_tile<G>(U, F, g, a.gc, ty0, tx0, s_at(a.fc, (size_t)c * a.gc.plane, a.sf), a.sf, a.fout);
 }
 
 // Up: u += P u_{l+1}, nu2 sweeps, write u. On the finest level instead:
@@ -733,9 +826,10 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
   const int ry0 = ty0 - G::HY, rx0 = tx0 - G::HX;
   const int cy0 = (ry0 >> 1) - 1, cx0 = (rx0 >> 1) - 1;
-  load_tile<G>(F, rhs_of(a, k) + (size_t)c * g.plane, g, ry0, rx0, rhs_offset(a, ctrl, k, c));
-  load_tile<G>(U, a.u + (size_t)c * g.plane, g, ry0, rx0);
-  load_coarse<G>(EC, a.uc + (size_t)c * a.gc.plane, a.gc, cy0, cx0);
+  const Rhs rh = rhs_of(a, ctrl, k, c);
+  load_tile<G>(F, rh.src, rh.sf, g, ry0, rx0, rh.off, rh.scale);
+  load_tile<G>(U, s_at(a.u, (size_t)c * g.plane, a.sf), a.sf, g, ry0, rx0, 0.f, 1.f);
+  load_coarse<G>(EC, s_at(a.uc, (size_t)c * a.gc.plane, a.sf), a.sf, a.gc, cy0, cx0);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
   prolong_tile<G>(U, EC, g, a.gc, ry0, rx0, cy0, cx0);
@@ -746,13 +840,14 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
     __syncthreads();
   }
   if (!a.level0) {
-    store_tile<G>(U, a.uo + (size_t)c * g.plane, g, ty0, tx0);
+    store_tile<G>(U, s_at(a.uo, (size_t)c * g.plane, a.sf), a.sf, g, ty0, tx0);
     return;
   }
   const size_t cb = (size_t)c * g.plane;
   float *uh = a.uhi + cb, *ul = a.ulo + cb, *rn = a.rb[k & 1] + cb;
+  const float inv_s = 1.f / rh.scale;  // exact: a power of two
   if (vec4_ok(g)) {
-    finest_epilogue4<G>(U, F, g, ty0, tx0, k, uh, ul, rn, ctrl, c);
+    finest_epilogue4<G>(U, F, g, ty0, tx0, k, uh, ul, rn, ctrl, c, inv_s);
     return;
   }
   constexpr int NY = G::TY / kBY, NX = G::TX / kBX;
@@ -778,11 +873,11 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
       const size_t p = (size_t)gy * g.W + gx;
       const int yy = y + G::HY, xx = x + G::HX;
       float hi = vh[i][j], lo = vl[i][j];
-      ds_add(hi, lo, at<G>(U, yy, xx));
+      ds_add(hi, lo, at<G>(U, yy, xx) * inv_s);
       uh[p] = hi;
       ul[p] = lo;
       su += hi + lo;
-      const float r = tile_residual<G>(U, F, g, yy, xx, gy, gx);
+      const float r = tile_residual<G>(U, F, g, yy, xx, gy, gx) * inv_s;
       rn[p] = r;
       rn2 = fmaf(r, r, rn2);
     }
@@ -822,8 +917,10 @@ struct TailArgs {
   int off_minv;              // the staged coarse inverse (doubles), or -1: read from global
   int off_fd;                // -f of the coarsest level in FP64
   int n;                     // levels in the tail (>= 1)
-  const float *f_top;        // right-hand side of level t [C][plane]
-  float *u_top;              // correction of level t [C][plane] (output)
+  const void *f_top;         // right-hand side of level t times 4^-t [C][plane] (storage sf)
+  void *u_top;               // correction of level t [C][plane] (output, storage sf)
+  int sf;                    // GDGS_STORAGE_*
+  float fin;                 // 4^t
   const double *Minv;        // [nc][nc] inverse of -L + 11^T / nc on the coarsest level
   int nu1, nu2;
   float omega;
@@ -995,14 +1092,14 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
 
   {  // right-hand side of the top level and the coarse inverse: loads first
     const TailLevel t = tail_level_at(S, a, 0);
-    const float *src = a.f_top + (size_t)c * a.lv[0].plane;
+    const void *src = s_at(a.f_top, (size_t)c * a.lv[0].plane, a.sf);
     const int np = (int)a.lv[0].plane;
     for (int q0 = tid; q0 < np; q0 += 4 * kTailThreads) {
       float v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int q = q0 + j * kTailThreads;
-        v[j] = q < np ? __ldg(src + q) : 0.f;
+        v[j] = q < np ? s_ld(src, q, a.sf) * a.fin : 0.f;
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -1111,8 +1208,8 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
   }
   {
     const TailLevel t = tail_level_at(S, a, 0);
-    float *dst = a.u_top + (size_t)c * a.lv[0].plane;
-    for (int q = tid; q < a.lv[0].plane; q += kTailThreads) dst[q] = t.u[q];
+    void *dst = s_at(a.u_top, (size_t)c * a.lv[0].plane, a.sf);
+    for (int q = tid; q < a.lv[0].plane; q += kTailThreads) s_st(dst, q, t.u[q], a.sf);
   }
 }
 
@@ -1146,6 +1243,16 @@ __device__ unsigned long long digest(const double *A, int n2) {
 // Builds and inverts M = -L + 11^T / n of the coarsest grid in FP64 (SPD, so
 // Gauss-Jordan without pivoting is stable), unless the cached one in the
 // workspace matches both the grid (tag) and its own digest.
+// The power of two s with s * rms(r) in [0.5, 1): cycle k works on s_k r_k.
+__device__ __forceinline__ float residual_scale(double rnorm2, long long cells) {
+  const double rms = sqrt(rnorm2 / (double)(cells > 0 ? cells : 1));
+  if (!(rms > 0.0) || !(rms < 1e300)) return 1.f;
+  int e = 0;
+  frexp(rms, &e);
+  e = max(-120, min(120, e));
+  return ldexpf(1.f, -e);
+}
+
 __global__ void __launch_bounds__(1024)
 coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl *ctrl, int C,
                     long long npx) {
@@ -1160,6 +1267,7 @@ coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl
       r2 += fmax(ctrl->rho_sq[c] - ctrl->rho_sum[c] * m, 0.0);
     }
     ctrl->rnorm2[0] = r2;
+    ctrl->escale[0] = residual_scale(r2, (long long)C * npx);
   }
   if (threadIdx.x == 0) {
     const CoarseTag t = *tag;
@@ -1321,8 +1429,9 @@ __device__ unsigned long long g_graph_kernels = 0;
 // End of cycle k: stop once ||r_{k+1}|| <= rtol ||rho||, advance the cycle
 // index, and (inside a graph) set the loop condition.
 __global__ void advance_kernel(Ctrl *ctrl, int k_in, cudaGraphConditionalHandle h, int in_graph,
-                               unsigned kernels_per_cycle) {
+                               unsigned kernels_per_cycle, long long cells) {
   const int k = k_in >= 0 ? k_in : ctrl->iter;
+  if (k + 1 <= kMaxCycles) ctrl->escale[k + 1] = residual_scale(ctrl->rnorm2[k + 1], cells);
   if (!ctrl->stopped) {
     const double thr = ctrl->rtol * ctrl->rtol * ctrl->rnorm2[0];
     const double rk = ctrl->rnorm2[k + 1];
@@ -1432,17 +1541,21 @@ struct Cycle {
   Ctrl *ctrl;
   int C, nu1, nu2;
   float omega;
+  int storage;
   const double *Minv;
 
   LvArgs level(int l) const {
     LvArgs a{};
     a.g = p->lv[l];
     a.gc = p->lv[l + 1];
-    a.f = l > 0 ? (const float *)(ws + p->off_lf[l]) : nullptr;
-    a.u = (float *)(ws + (l > 0 ? p->off_lu[l] : p->off_e0));
-    a.uo = l > 0 ? (float *)(ws + p->off_luo[l]) : nullptr;
-    a.fc = (float *)(ws + p->off_lf[l + 1]);
-    a.uc = (const float *)(ws + p->off_luo[l + 1]);
+    a.f = l > 0 ? (const void *)(ws + p->off_lf[l]) : nullptr;
+    a.u = ws + (l > 0 ? p->off_lu[l] : p->off_e0);
+    a.uo = l > 0 ? (void *)(ws + p->off_luo[l]) : nullptr;
+    a.fc = ws + p->off_lf[l + 1];
+    a.uc = ws + p->off_luo[l + 1];
+    a.sf = storage;
+    a.fin = ldexpf(1.f, 2 * l);
+    a.fout = ldexpf(1.f, -2 * (l + 1));
     a.level0 = l == 0;
     a.rho = (const float *)(ws + p->off_rho);
     a.rb[0] = (float *)(ws + p->off_r[0]);
@@ -1461,8 +1574,10 @@ struct Cycle {
     a.n = p->levels - t;
     for (int i = 0; i < a.n; ++i) a.lv[i] = p->lv[t + i];
     tail_layout(a.lv, a.n, &a);
-    a.f_top = (const float *)(ws + p->off_lf[t]);
-    a.u_top = (float *)(ws + p->off_luo[t]);
+    a.f_top = ws + p->off_lf[t];
+    a.u_top = ws + p->off_luo[t];
+    a.sf = storage;
+    a.fin = ldexpf(1.f, 2 * t);
     a.Minv = Minv;
     a.nu1 = nu1;
     a.nu2 = nu2;
@@ -1517,7 +1632,8 @@ struct Cycle {
     }
     {
       LaunchScope ls_("mg_advance", st);
-      advance_kernel<<<1, 1, 0, st>>>(ctrl, k, h, in_graph, kernels());
+      advance_kernel<<<1, 1, 0, st>>>(ctrl, k, h, in_graph, kernels(),
+                                      (long long)C * p->lv[0].plane);
     }
     return cudaGetLastError();
   }
@@ -1534,13 +1650,14 @@ struct Cycle {
 struct GraphKey {
   int dev;
   const void *ws;
-  int C, H, W, nu1, nu2, max_cycles, levels;
+  int C, H, W, nu1, nu2, max_cycles, levels, storage;
   float omega;
   size_t off_rho, off_coarse, total;
   bool operator<(const GraphKey &o) const {
-    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, omega, off_rho, off_coarse,
-                    total) < std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles,
-                                      o.levels, o.omega, o.off_rho, o.off_coarse, o.total);
+    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, storage, omega, off_rho,
+                    off_coarse, total) <
+           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.levels, o.storage,
+                    o.omega, o.off_rho, o.off_coarse, o.total);
   }
 };
 
@@ -1681,6 +1798,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   cy.nu1 = a.nu1;
   cy.nu2 = a.nu2;
   cy.omega = a.omega;
+  cy.storage = a.storage;
   cy.Minv = Minv;
 
   if ((e = cy.prepare()) != cudaSuccess) return e;
@@ -1689,8 +1807,9 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const GraphKey key{dev,      ws,         a.C,    a.H,     a.W,       a.nu1, a.nu2,
-                       a.max_cycles, p.levels, a.omega, p.off_rho, p.off_coarse, p.total};
+    const GraphKey key{dev,       ws,      a.C,       a.H,          a.W,    a.nu1, a.nu2,
+                       a.max_cycles, p.levels, a.storage, a.omega, p.off_rho, p.off_coarse,
+                       p.total};
     if ((e = launch_cycle_graph(cy, key, st)) != cudaSuccess) return e;
   } else {
     // direct launches: every cycle is enqueued; once the advance kernel has

@@ -60,7 +60,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_abi.Gaussians) == 8 + 4 + 4 + 5 * 8
     assert ctypes.sizeof(_abi.Camera) == 17 * 4 + 8
     assert ctypes.sizeof(_abi.RasterOpts) == 24
-    assert ctypes.sizeof(_abi.SolverOpts) == 28
+    assert ctypes.sizeof(_abi.SolverOpts) == 32
     assert ctypes.sizeof(_abi.SolveStats) == 4 + 4 + 8 + 8 + 32 + 8 + 4 + 4
 
 

@@ -198,6 +198,57 @@ def test_identical_channels_give_identical_images_1080p(max_cycles):
         assert st["status"] == 0 and st["cycles"] <= 5, st
 
 
+STORAGES = {"f32": 0, "bf16": 1, "f16": 2}
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_poisson_16bit_storage_reaches_tolerance_1080p(storage):
+    """BF16 / FP16 storage of the multigrid corrections and coarse right-hand sides:
+    the FP32 residual recurrence refines the float-float iterate to rtol all the same."""
+    H, W = 1080, 1920
+    img0 = np.stack([S.image_from_gradients_test_image(H, W, seed=s) for s in range(3)])
+    maps = O.forward_gradients(img0).astype(np.float32)
+    img, st = gpu_poisson(maps, img0.mean(axis=(1, 2)), G.solver_opts(storage=STORAGES[storage]))
+    ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), img0.mean(axis=(1, 2)))
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    assert st["cycles"] <= 12
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_poisson_storage_4k_against_oracle(storage):
+    """The 4K grid (3840 x 2160, 10 levels) in every storage format, one channel,
+    against the exact DCT solve."""
+    H, W = 2160, 3840
+    img0 = S.image_from_gradients_test_image(H, W, seed=11)[None]
+    maps = O.forward_gradients(img0).astype(np.float32)
+    img, st = gpu_poisson(maps, [float(img0.mean())], G.solver_opts(storage=STORAGES[storage]))
+    ref = O.poisson_neumann(O.divergence(maps.astype(np.float64)), [float(img0.mean())])
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_render_view_16bit_storage(storage):
+    scene, cam = _small_prims(n=8000)
+    mean = [0.5, 0.5, 0.5]
+    img, st = _render(scene, cam, mean, sopts=G.solver_opts(storage=STORAGES[storage]))
+    ref, _, _ = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    assert img_err(img, ref)[1] <= IMG_TOL
+
+
+def test_storage_scaling_keeps_fp32_bitwise():
+    """The per-cycle power-of-two scaling is exact: FP32 storage gives the same bits
+    for a field and for the same field times 2^20 (then divided back)."""
+    rng = np.random.default_rng(17)
+    maps = rng.laplace(0, 0.1, (2, 2, 150, 211)).astype(np.float32)
+    a, sa = gpu_poisson(maps, [0.0, 0.0])
+    b, sb = gpu_poisson(maps * np.float32(2.0 ** 20), [0.0, 0.0])
+    assert sa["status"] == sb["status"] == 0 and sa["cycles"] == sb["cycles"]
+    assert np.array_equal(a * 2.0 ** 20, b)
+
+
 def test_poisson_zero_field_gives_mean():
     img, st = gpu_poisson(np.zeros((2, 2, 40, 50), np.float32), [0.25, 0.75])
     assert st["status"] == 0 and st["cycles"] == 0
