@@ -240,6 +240,20 @@ GDGS_API int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, c
                      const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts,
                      float *image, void *ws, size_t ws_bytes, void *stream);
 
+/* gdgs_render_view with the camera read from device memory when the kernels run
+ * (no paper counterpart: a serving variant). `cam` (host) gives the image size the
+ * workspace is planned for; its pose and intrinsics are ignored. `cam_dev` (device,
+ * one gdgs_camera, 4-byte aligned) supplies world_to_cam, fx, fy, cx, cy and
+ * near_plane; its width and height must equal cam's. Because no camera value is
+ * baked into the launches, a CUDA graph captured from one call (the multigrid
+ * cycle loop is then recorded as a conditional WHILE node) replays correctly for
+ * any camera written to cam_dev before the replay. Errors as gdgs_render_view. */
+GDGS_API int gdgs_render_view_devcam(const gdgs_gaussians *g, const gdgs_camera *cam,
+                                     const gdgs_camera *cam_dev, const float *mean,
+                                     const gdgs_raster_opts *ropts,
+                                     const gdgs_solver_opts *sopts, float *image, void *ws,
+                                     size_t ws_bytes, void *stream);
+
 /* Wait for `stream`, then read the device status word and statistics of the last
  * call that used `ws`. `stats` (host) may be NULL. Returns the device status (or
  * GDGS_ERR_CUDA if the synchronisation itself failed). */

@@ -165,6 +165,25 @@ def render_view(g: DeviceGaussians, cam, mean, image, ws, ropts=None, sopts=None
            "gdgs_render_view")
 
 
+def camera_bytes(cam) -> bytes:
+    """The gdgs_camera struct of `cam` as bytes (to fill a device camera buffer)."""
+    import ctypes
+    c = camera_struct(cam)
+    return ctypes.string_at(ctypes.addressof(c), ctypes.sizeof(c))
+
+
+def render_view_devcam(g: DeviceGaussians, cam, cam_dev, mean, image, ws, ropts=None, sopts=None,
+                       stream=None) -> None:
+    """render_view with the pose and intrinsics read from `cam_dev` (a device tensor
+    holding one gdgs_camera, see camera_bytes) when the kernels run; `cam` gives
+    the image size. A CUDA graph captured from this call replays for any camera."""
+    gs = g.struct()
+    _check(_lib().gdgs_render_view_devcam(gs, camera_struct(cam), _ptr(cam_dev),
+                                          _mean_array(mean, g.channels), ropts, sopts,
+                                          _ptr(image), _ptr(ws), ws.numel(), _stream(stream)),
+           "gdgs_render_view_devcam")
+
+
 def sync_status(ws, stream=None, raise_on_error: bool = False) -> dict:
     st = _abi.SolveStats()
     code = _lib().gdgs_sync_status(_ptr(ws), st, _stream(stream))

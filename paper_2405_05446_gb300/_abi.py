@@ -93,6 +93,10 @@ PROTOTYPES = {
     "gdgs_render_view": (ctypes.c_int, [ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
                                         ctypes.POINTER(_f), ctypes.POINTER(RasterOpts),
                                         ctypes.POINTER(SolverOpts), _p, _p, ctypes.c_size_t, _p]),
+    "gdgs_render_view_devcam": (ctypes.c_int, [ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
+                                               _p, ctypes.POINTER(_f), ctypes.POINTER(RasterOpts),
+                                               ctypes.POINTER(SolverOpts), _p, _p, ctypes.c_size_t,
+                                               _p]),
     "gdgs_sync_status": (ctypes.c_int, [_p, ctypes.POINTER(SolveStats), _p]),
     "gdgs_poisson_reconstruct_static": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(_f),
                                                        ctypes.POINTER(SolverOpts), _p,

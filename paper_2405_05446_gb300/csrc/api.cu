@@ -218,9 +218,12 @@ int to_status(cudaError_t e) { return e == cudaSuccess ? GDGS_OK : GDGS_ERR_CUDA
 // Steps 1-2 into `maps` (and `mask` when use_mask).
 cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
                         const gdgs_raster_opts &ro, const Plan &p, char *ws, float *maps,
-                        uint8_t *mask, bool use_mask, cudaStream_t st) {
+                        uint8_t *mask, bool use_mask, cudaStream_t st,
+                        const gdgs_camera *cam_dev = nullptr) {
   Ctrl *ctrl = (Ctrl *)(ws + p.off_ctrl);
-  cudaError_t e = launch_project(project_args(g, cam, ro, p, ws), st);
+  ProjectArgs pa = project_args(g, cam, ro, p, ws);
+  pa.cam_dev = cam_dev;
+  cudaError_t e = launch_project(pa, st);
   if (e != cudaSuccess) return e;
   uint32_t *hist = (uint32_t *)(ws + p.off_hist);
   uint2 *range = (uint2 *)(ws + p.off_range);
@@ -443,9 +446,10 @@ int gdgs_poisson_reconstruct_rho(const float *rho, const uint8_t *tile_mask, int
                         ws_bytes, stream);
 }
 
-int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const float *mean,
-                     const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts, float *image,
-                     void *ws, size_t ws_bytes, void *stream) {
+static int render_view_impl(const gdgs_gaussians *g, const gdgs_camera *cam,
+                            const gdgs_camera *cam_dev, const float *mean,
+                            const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts,
+                            float *image, void *ws, size_t ws_bytes, void *stream) {
   int s;
   if ((s = check_gaussians(g)) || (s = check_camera(cam))) return s;
   if (!image || !mean || !aligned(image, 16)) return GDGS_ERR_INVALID_ARG;
@@ -461,7 +465,7 @@ int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const floa
   if (cudaMemsetAsync(w + p.off_ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return GDGS_ERR_CUDA;
   uint8_t *mask = (uint8_t *)(w + p.off_mask);
   float *maps = (float *)(w + p.off_maps);
-  cudaError_t e = raster_path(g, cam, ro, p, w, maps, mask, true, st);
+  cudaError_t e = raster_path(g, cam, ro, p, w, maps, mask, true, st, cam_dev);
   if (e != cudaSuccess) return GDGS_ERR_CUDA;
   PoissonArgs a{};
   a.maps = maps;
@@ -484,6 +488,20 @@ int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const floa
   a.ws = w;
   a.ctrl = (Ctrl *)(w + p.off_ctrl);
   return to_status(run_poisson(a, st));
+}
+
+int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, const float *mean,
+                     const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts, float *image,
+                     void *ws, size_t ws_bytes, void *stream) {
+  return render_view_impl(g, cam, nullptr, mean, ropts, sopts, image, ws, ws_bytes, stream);
+}
+
+int gdgs_render_view_devcam(const gdgs_gaussians *g, const gdgs_camera *cam,
+                            const gdgs_camera *cam_dev, const float *mean,
+                            const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts,
+                            float *image, void *ws, size_t ws_bytes, void *stream) {
+  if (!cam_dev || !aligned(cam_dev, 4)) return GDGS_ERR_INVALID_ARG;
+  return render_view_impl(g, cam, cam_dev, mean, ropts, sopts, image, ws, ws_bytes, stream);
 }
 
 int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream) {

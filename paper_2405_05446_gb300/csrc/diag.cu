@@ -46,6 +46,9 @@ void diag_set_capturing(bool on) { t_capturing = on; }
 void diag_before(const char *name, cudaStream_t st) {
   t_open = -1;
   if (t_capturing) return;  // counted when the graph runs
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return;  // recorded into a caller's graph: runs (and is counted by it) at replay
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_profiling.load(std::memory_order_acquire)) return;
   std::lock_guard<std::mutex> lk(g_mu);

@@ -121,6 +121,7 @@ struct ProjectArgs {
   float w2c[12];
   float fx, fy, cx, cy, znear;
   int W, H, tiles_x, tiles_y;
+  const gdgs_camera *cam_dev;  // when set, w2c .. znear are read from it on the device
   float alpha_min, dilation, exp_coef;
   // outputs (workspace)
   float4 *smean;   // mx_hi, my_hi, mx_lo, my_lo

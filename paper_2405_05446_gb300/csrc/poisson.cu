@@ -1740,6 +1740,45 @@ cudaError_t launch_cycle_graph(const Cycle &cy, const GraphKey &key, cudaStream_
   return cudaGraphLaunch(it->second.exec, st);
 }
 
+// While `st` is being captured into a graph (a caller recording a whole view):
+// add the cycle loop to that graph as a conditional WHILE node whose body is one
+// V-cycle, recorded on a helper stream, and make the rest of the capture depend
+// on it. The loop then runs exactly as many cycles as it needs at replay.
+cudaError_t capture_cycle_loop(const Cycle &cy, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, edges, nd, &np);
+  if (e != cudaSuccess) return e;
+  static thread_local cudaStream_t helper = nullptr;
+  if (!helper && (e = cudaStreamCreateWithFlags(&helper, cudaStreamNonBlocking)) != cudaSuccess) {
+    helper = nullptr;
+    return e;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(helper, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  const cudaError_t le = cy.launch(-1, h, 1, helper);
+  e = cudaStreamEndCapture(helper, &body);
+  if (le != cudaSuccess) return le;
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 }  // namespace
 
 unsigned long long graph_kernel_count() {
@@ -1804,7 +1843,9 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   if ((e = cy.prepare()) != cudaSuccess) return e;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
-  if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
+  if (cap == cudaStreamCaptureStatusActive && graphs_enabled() && !diag_profiling()) {
+    if ((e = capture_cycle_loop(cy, st)) != cudaSuccess) return e;
+  } else if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
     int dev = 0;
     cudaGetDevice(&dev);
     const GraphKey key{dev,       ws,      a.C,       a.H,          a.W,    a.nu1, a.nu2,

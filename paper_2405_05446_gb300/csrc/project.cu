@@ -24,6 +24,16 @@ namespace gdgs {
 namespace {
 
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
+  if (a.cam_dev) {  // camera from device memory (a graph replays for any camera)
+    const gdgs_camera *cd = a.cam_dev;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) a.w2c[j] = __ldg(&cd->world_to_cam[j]);
+    a.fx = __ldg(&cd->fx);
+    a.fy = __ldg(&cd->fy);
+    a.cx = __ldg(&cd->cx);
+    a.cy = __ldg(&cd->cy);
+    a.znear = __ldg(&cd->near_plane);
+  }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool visible = false;
   if (i < a.n) {
