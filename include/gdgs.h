@@ -254,6 +254,38 @@ GDGS_API int gdgs_render_view_devcam(const gdgs_gaussians *g, const gdgs_camera 
                                      const gdgs_solver_opts *sopts, float *image, void *ws,
                                      size_t ws_bytes, void *stream);
 
+/* Gradients of a loss with respect to the Gaussians (device arrays, the layouts of
+ * gdgs_gaussians; overwritten). */
+typedef struct gdgs_gaussian_grads {
+  float *d_mean;     /* [n][3] */
+  float *d_scale;    /* [n][3] */
+  float *d_quat;     /* [n][4] */
+  float *d_opacity;  /* [n]    */
+  float *d_attr;     /* [n][channels][2] (gradient) or [n][channels] (Laplacian) */
+} gdgs_gaussian_grads;
+
+/* Backward of gdgs_render_view (Algorithm 1's render steps differentiated; the
+ * training loop itself is not part of this library): given d_image = d loss /
+ * d image (device [channels][height][width]), write d loss / d (mean, scale,
+ * quat, opacity, attribute) into `grads`.
+ *   ws: the workspace of the gdgs_render_view call of the same (g, cam, ropts,
+ *   sopts) whose image is being differentiated, not used by any call since (its
+ *   projected splats, sorted pairs, tile lists and rho are read; its gradient-map
+ *   region is reused).
+ *   ws_adj: a second workspace of gdgs_workspace_size(0, channels, width,
+ *   height, NULL, sopts) bytes for the adjoint solve (L is symmetric: the same
+ *   zero-mean Neumann solve, applied to d_image); gdgs_sync_status(ws_adj, ...)
+ *   reports its convergence.
+ * The alpha tests, the T_min stop, culls, the depth order and the threshold's
+ * decision are piecewise constant and contribute no derivative. Errors as
+ * gdgs_render_view; GDGS_ERR_WORKSPACE if either workspace is too small. */
+GDGS_API int gdgs_render_view_backward(const gdgs_gaussians *g, const gdgs_camera *cam,
+                                       const gdgs_raster_opts *ropts,
+                                       const gdgs_solver_opts *sopts, const float *d_image,
+                                       const gdgs_gaussian_grads *grads, void *ws,
+                                       size_t ws_bytes, void *ws_adj, size_t ws_adj_bytes,
+                                       void *stream);
+
 /* Wait for `stream`, then read the device status word and statistics of the last
  * call that used `ws`. `stats` (host) may be NULL. Returns the device status (or
  * GDGS_ERR_CUDA if the synchronisation itself failed). */

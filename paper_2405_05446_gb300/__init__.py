@@ -184,6 +184,23 @@ def render_view_devcam(g: DeviceGaussians, cam, cam_dev, mean, image, ws, ropts=
            "gdgs_render_view_devcam")
 
 
+def render_view_backward(g: DeviceGaussians, cam, d_image, ws, ws_adj, ropts=None, sopts=None,
+                         stream=None) -> dict:
+    """d loss / d (mean, scale, quat, opacity, grad) from d_image = d loss / d image, for
+    the gdgs_render_view call that last used `ws` (same g, cam and options).
+    ws_adj: a Poisson workspace (workspace_size(0, ...)) for the adjoint solve."""
+    import torch
+    gr = {k: torch.empty_like(getattr(g, k)) for k in ("mean", "scale", "quat", "opacity", "grad")}
+    gg = _abi.GaussianGrads(_ptr(gr["mean"]), _ptr(gr["scale"]), _ptr(gr["quat"]),
+                            _ptr(gr["opacity"]), _ptr(gr["grad"]))
+    d_image = d_image.contiguous()
+    _check(_lib().gdgs_render_view_backward(g.struct(), camera_struct(cam), ropts, sopts,
+                                            _ptr(d_image), gg, _ptr(ws), ws.numel(), _ptr(ws_adj),
+                                            ws_adj.numel(), _stream(stream)),
+           "gdgs_render_view_backward")
+    return gr
+
+
 def sync_status(ws, stream=None, raise_on_error: bool = False) -> dict:
     st = _abi.SolveStats()
     code = _lib().gdgs_sync_status(_ptr(ws), st, _stream(stream))

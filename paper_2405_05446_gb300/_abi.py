@@ -56,6 +56,10 @@ class SolverOpts(ctypes.Structure):
                 ("storage", _i32)]
 
 
+class GaussianGrads(ctypes.Structure):
+    _fields_ = [("d_mean", _p), ("d_scale", _p), ("d_quat", _p), ("d_opacity", _p), ("d_attr", _p)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("status", _i32), ("cycles", _i32), ("rel_residual", ctypes.c_double),
                 ("rho_norm", ctypes.c_double), ("mean_set", ctypes.c_double * MAX_CHANNELS),
@@ -97,6 +101,10 @@ PROTOTYPES = {
                                                _p, ctypes.POINTER(_f), ctypes.POINTER(RasterOpts),
                                                ctypes.POINTER(SolverOpts), _p, _p, ctypes.c_size_t,
                                                _p]),
+    "gdgs_render_view_backward": (ctypes.c_int, [ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
+                                                 ctypes.POINTER(RasterOpts), ctypes.POINTER(SolverOpts),
+                                                 _p, ctypes.POINTER(GaussianGrads), _p, ctypes.c_size_t,
+                                                 _p, ctypes.c_size_t, _p]),
     "gdgs_sync_status": (ctypes.c_int, [_p, ctypes.POINTER(SolveStats), _p]),
     "gdgs_poisson_reconstruct_static": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(_f),
                                                        ctypes.POINTER(SolverOpts), _p,

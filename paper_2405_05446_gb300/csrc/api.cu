@@ -107,6 +107,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
     p->off_hist = cv.take(4 * 256 * (size_t)(p->radix_blocks_max + 1));
     p->off_blocksum = cv.take(8 * (size_t)(p->radix_blocks_max + 2));
     p->off_maps = cv.take(4 * (size_t)C * 2 * W * H);
+    p->off_dsplat = cv.take(24 * (size_t)n);
   }
   p->off_range = cv.take(8 * (size_t)p->T);
   p->off_active = cv.take(4 * (size_t)p->T);
@@ -502,6 +503,113 @@ int gdgs_render_view_devcam(const gdgs_gaussians *g, const gdgs_camera *cam,
                             float *image, void *ws, size_t ws_bytes, void *stream) {
   if (!cam_dev || !aligned(cam_dev, 4)) return GDGS_ERR_INVALID_ARG;
   return render_view_impl(g, cam, cam_dev, mean, ropts, sopts, image, ws, ws_bytes, stream);
+}
+
+int gdgs_render_view_backward(const gdgs_gaussians *g, const gdgs_camera *cam,
+                              const gdgs_raster_opts *ropts, const gdgs_solver_opts *sopts,
+                              const float *d_image, const gdgs_gaussian_grads *grads, void *ws,
+                              size_t ws_bytes, void *ws_adj, size_t ws_adj_bytes, void *stream) {
+  int s;
+  if ((s = check_gaussians(g)) || (s = check_camera(cam))) return s;
+  if (!d_image || !grads || !grads->d_mean || !grads->d_scale || !grads->d_quat ||
+      !grads->d_opacity || !grads->d_attr)
+    return GDGS_ERR_INVALID_ARG;
+  const gdgs_raster_opts ro = ropts_or_default(ropts);
+  const gdgs_solver_opts so = sopts_or_default(sopts);
+  Plan p, pa;
+  if (!make_plan(g->n, g->channels, cam->width, cam->height, ro, so, &p) ||
+      !make_plan(0, g->channels, cam->width, cam->height, ro, so, &pa))
+    return GDGS_ERR_INVALID_ARG;
+  if ((s = check_ws(ws, ws_bytes, p)) || (s = check_ws(ws_adj, ws_adj_bytes, pa))) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)ws, *wa = (char *)ws_adj;
+  const int C = g->channels, Q = attr_floats(g);
+  const size_t n = (size_t)g->n, plane = (size_t)cam->width * cam->height;
+  // gradients accumulate (atomics) or are written per Gaussian: clear first
+  if (cudaMemsetAsync(grads->d_attr, 0, 4 * n * Q, st) != cudaSuccess ||
+      (n && cudaMemsetAsync(w + p.off_dsplat, 0, 24 * n, st) != cudaSuccess) ||
+      cudaMemsetAsync(wa + pa.off_ctrl, 0, sizeof(Ctrl), st) != cudaSuccess)
+    return GDGS_ERR_CUDA;
+  // 1. d rho = the zero-mean solve of d image (L symmetric), into the forward
+  //    workspace's correction array (the multigrid scratch is not read below)
+  float *rbar = (float *)(w + p.off_e0);
+  PoissonArgs a{};
+  a.maps = d_image;
+  a.input_is_rho = 1;
+  a.threshold = 0.f;
+  a.mask = nullptr;
+  a.C = C;
+  a.H = cam->height;
+  a.W = cam->width;
+  a.tiles_x = pa.tiles_x;
+  for (int c = 0; c < GDGS_MAX_CHANNELS; ++c) a.mean[c] = 0.f;
+  a.image = rbar;
+  a.nu1 = so.nu1;
+  a.nu2 = so.nu2;
+  a.omega = so.omega;
+  a.storage = so.storage;
+  a.max_cycles = so.max_cycles;
+  a.rtol = so.rtol;
+  a.plan = &pa;
+  a.ws = wa;
+  a.ctrl = (Ctrl *)(wa + pa.off_ctrl);
+  cudaError_t e = run_poisson(a, st);
+  if (e != cudaSuccess) return to_status(e);
+  if (n == 0) return GDGS_OK;
+  // 2. through the threshold and the divergence into d maps
+  DivAdjArgs d{};
+  d.rbar = rbar;
+  d.rho_fwd = so.rho_threshold > 0.f ? (const float *)(w + p.off_rho) : nullptr;
+  d.mask = (const uint8_t *)(w + p.off_mask);
+  d.input_is_rho = g->attribute == GDGS_ATTR_LAPLACIAN;
+  d.C = C;
+  d.H = cam->height;
+  d.W = cam->width;
+  d.tiles_x = p.tiles_x;
+  d.mbar = (float *)(w + p.off_maps);
+  if ((e = launch_divergence_adjoint(d, st)) != cudaSuccess) return to_status(e);
+  // 3. the composite, tile by tile, back to front
+  int tbits = 0;
+  while ((1 << tbits) < p.T) ++tbits;
+  const bool alt = ((tbits + 7) / 8) % 2 == 1;  // the pair sort's passes swap buffers
+  RasterBwdArgs r{};
+  r.smean = (const float4 *)(w + p.off_smean);
+  r.sconic = (const float4 *)(w + p.off_sconic);
+  r.attr = g->grad;
+  r.pval = (const uint32_t *)(w + p.off_pval[alt ? 1 : 0]);
+  r.range = (const uint2 *)(w + p.off_range);
+  r.active = (const uint32_t *)(w + p.off_active);
+  r.Q = Q;
+  r.W = cam->width;
+  r.H = cam->height;
+  r.tiles_x = p.tiles_x;
+  r.T = p.T;
+  r.alpha_min = ro.alpha_min;
+  r.alpha_max = ro.alpha_max;
+  r.t_min = ro.t_min;
+  r.mbar = (const float *)(w + p.off_maps);
+  r.dsplat = (float *)(w + p.off_dsplat);
+  r.dattr = grads->d_attr;
+  r.ctrl = (Ctrl *)(w + p.off_ctrl);
+  if ((e = launch_raster_backward(r, st)) != cudaSuccess) return to_status(e);
+  // 4. the projection
+  ProjBwdArgs pb{};
+  pb.mean = g->mean;
+  pb.scale = g->scale;
+  pb.quat = g->quat;
+  pb.n = g->n;
+  memcpy(pb.w2c, cam->world_to_cam, sizeof(pb.w2c));
+  pb.fx = cam->fx;
+  pb.fy = cam->fy;
+  pb.dilation = ro.dilation;
+  pb.exp_coef = ro.exp_coef;
+  pb.dsplat = (const float *)(w + p.off_dsplat);
+  pb.d_mean = grads->d_mean;
+  pb.d_scale = grads->d_scale;
+  pb.d_quat = grads->d_quat;
+  pb.d_opacity = grads->d_opacity;
+  (void)plane;
+  return to_status(launch_project_backward(pb, st));
 }
 
 int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *stream) {

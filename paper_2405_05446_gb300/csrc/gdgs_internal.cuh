@@ -88,6 +88,7 @@ struct Plan {
   size_t off_pkey[2], off_pval[2];                     // pairs [pair_cap]
   size_t off_range, off_active, off_mask;              // per tile
   size_t off_maps;                                     // [C][2][H][W]
+  size_t off_dsplat;                                   // backward: [n][6]
   size_t off_rho, off_uhi, off_ulo, off_e0, off_r[2];  // level 0 [C][H][W]
   size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1: down-pass u, f
   size_t off_luo[kMaxLevels];                          // levels >= 1: up-pass u (never in place)
@@ -192,5 +193,42 @@ struct PoissonArgs {
   Ctrl *ctrl;
 };
 cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- backward
+struct DivAdjArgs {
+  const float *rbar;     // d loss / d rho [C][H][W]
+  const float *rho_fwd;  // the forward's thresholded rho (null: no threshold)
+  const uint8_t *mask;   // forward tile mask (null: none)
+  int input_is_rho;      // Laplacian attribute: maps are rho itself
+  int C, H, W, tiles_x;
+  float *mbar;           // d loss / d maps [Q][H][W]
+};
+cudaError_t launch_divergence_adjoint(const DivAdjArgs &a, cudaStream_t st);
+
+struct RasterBwdArgs {
+  const float4 *smean, *sconic;
+  const float *attr;        // per-Gaussian attribute [n][Q]
+  const uint32_t *pval;     // the forward's sorted pairs
+  const uint2 *range;
+  const uint32_t *active;
+  int Q, W, H, tiles_x, T;
+  float alpha_min, alpha_max, t_min;
+  const float *mbar;        // d loss / d maps [Q][H][W]
+  float *dsplat;            // [n][6]: centre x, y; stored conic A, B, C; opacity (accumulated)
+  float *dattr;             // [n][Q] (accumulated)
+  Ctrl *ctrl;
+};
+cudaError_t launch_raster_backward(const RasterBwdArgs &a, cudaStream_t st);
+
+struct ProjBwdArgs {
+  const float *mean, *scale, *quat;
+  int64_t n;
+  float w2c[12];
+  float fx, fy;
+  float dilation, exp_coef;
+  const float *dsplat;
+  float *d_mean, *d_scale, *d_quat, *d_opacity;
+};
+cudaError_t launch_project_backward(const ProjBwdArgs &a, cudaStream_t st);
 
 }  // namespace gdgs
