@@ -265,13 +265,85 @@ def run_serving(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_training(args, rank, world):
+    """Forward + backward throughput: 500k Gaussians, 8 views at 1280x720 on a ring of
+    radius 3; targets are the FP64 oracle's renders of a perturbed copy of the scene
+    (mean + N(0, 0.01), attribute + N(0, 0.02)). A step renders the 8 views,
+    back-propagates the mean squared error through the library's backward and
+    takes an Adam step on every Gaussian parameter."""
+    import numpy as np
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2405_05446_gb300 import build as B
+    B.build()
+    import paper_2405_05446_gb300 as G
+    from paper_2405_05446_gb300 import autograd as A
+    from paper_2405_05446_gb300 import scenes as S
+    import oracle as O
+    O.build()
+    cams = S.ring_cameras(8, 3.0, 1280, 720)
+    scene = S.primitives_scene(0, n=500_000, orient_camera=cams[0])
+    rng = np.random.default_rng(1234)
+    pert = S.Scene((scene.mean + rng.normal(0, 0.01, scene.mean.shape)).astype(np.float32), scene.scale,
+                   scene.quat, scene.opacity,
+                   (scene.grad + rng.normal(0, 0.02, scene.grad.shape)).astype(np.float32))
+    mean = [0.5, 0.5, 0.5]
+    t0 = time.perf_counter()
+    targets = [torch.as_tensor(O.render_view(pert, c, mean, nthreads=os.cpu_count())[0], dtype=torch.float32).cuda()
+               for c in cams]
+    t_oracle = time.perf_counter() - t0
+    ropts = G.raster_opts()
+    params = [torch.tensor(np.asarray(getattr(scene, k)), device="cuda", requires_grad=True)
+              for k in ("mean", "scale", "quat", "opacity", "grad")]
+    opt = torch.optim.Adam(params, lr=1e-4)
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        loss = 0.0
+        for c, tgt in zip(cams, targets):
+            img = A.render_view(*params, c, mean, ropts)
+            l = ((img - tgt) ** 2).mean()
+            l.backward()
+            loss += float(l.detach())
+        opt.step()
+        return loss / len(cams)
+
+    for _ in range(max(args.warmup, 3)):
+        first = step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    losses = [step() for _ in range(args.steps)]
+    b.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b)
+    views = 8 * args.steps
+    line = {"metric": "1280x720 views/s, forward + backward (500k Gaussians)",
+            "value": views / (ms / 1e3), "unit": "views/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "train720p", "gaussians": scene.n, "views_per_step": 8,
+                       "size": [1280, 720], "optimizer": "Adam lr 1e-4", "global_batch": 8,
+                       "seq_len": None, "parallelism": "replicas x1",
+                       "l2": "not flushed (each step touches ~2 GB)"},
+            "loss_first_warmup": first, "loss_last": losses[-1], "oracle_targets_s": t_oracle,
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gdgs", choices=["gdgs", "reference"])
-    ap.add_argument("--workload", default="prims1080p", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="prims1080p",
+                    choices=sorted(WORKLOADS) + ["serving", "train720p"])
     ap.add_argument("--rates", default="200,500,1000,2000",
                     help="serving: offered request rates (req/s), one timed pass each")
     ap.add_argument("--requests", type=int, default=4000, help="serving: requests per rate")
@@ -291,6 +363,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank, world)
+        return
+    if args.workload == "train720p":
+        run_training(args, rank, world)
         return
 
     import numpy as np
