@@ -427,11 +427,10 @@ def main():
     clocks = sampler.stop()
     per = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(per)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = world * args.steps / (total_ms_max / 1e3)
+    from paper_2405_05446_gb300 import replicas
+    agg = replicas.aggregate(float(args.steps), total_ms / 1e3, device=dev)  # replicas: no data collective
+    total_ms_max = 1e3 * agg["seconds"]
+    value = agg["value"]
     st = r.stats()
 
     # end to end through the public API with host buffers: pinned H2D of the scene,
@@ -456,10 +455,7 @@ def main():
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps / (float(te.item()) / 1e3)
+    e2e_value = replicas.aggregate(float(e2e_steps), e2e_ms / 1e3, device=dev)["value"]
 
     # per-kernel CUDA-event times (outside the timed region). Profiling launches
     # the cycle loop directly; max_cycles = the observed count keeps it free of
