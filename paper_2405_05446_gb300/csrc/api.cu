@@ -105,7 +105,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
       p->off_pval[b] = cv.take(4 * (size_t)p->pair_cap);
     }
     p->off_hist = cv.take(4 * 256 * (size_t)(p->radix_blocks_max + 1));
-    p->off_blocksum = cv.take(8 * (size_t)(p->radix_blocks_max + 2));
+    p->off_blocksum = cv.take(8 * (size_t)((n + kBinBlock - 1) / kBinBlock + 2));
     p->off_maps = cv.take(4 * (size_t)C * 2 * W * H);
     p->off_dsplat = cv.take(24 * (size_t)n);
   }
@@ -244,6 +244,9 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
     BinArgs b{};
     b.order = order;
     b.rect = (const uint2 *)(ws + p.off_rect);
+    b.smean = (const float4 *)(ws + p.off_smean);
+    b.sconic = (const float4 *)(ws + p.off_sconic);
+    b.alpha_min = ro.alpha_min;
     b.n = g->n;
     b.tiles_x = p.tiles_x;
     b.T = p.T;

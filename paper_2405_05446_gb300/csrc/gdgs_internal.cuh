@@ -16,6 +16,7 @@ constexpr int kMaxLevels = 24;          // bound on multigrid levels
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;         // keys per thread per radix block
 constexpr int kRadixBlock = kRadixThreads * kRadixItems;
+constexpr int kBinBlock = 256;  // Gaussians per block of the pair count and emission
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
 // Device control block at offset 0 of every workspace. Zeroed at the start of
@@ -149,10 +150,12 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 struct BinArgs {
   const uint32_t *order;   // Gaussian indices in depth order [n]
   const uint2 *rect;
+  const float4 *smean, *sconic;  // projected splats (ellipse test of each tile of the rect)
+  float alpha_min;
   int64_t n;
   int tiles_x, T;
   unsigned pair_cap;
-  unsigned long long *blocksum;  // [ceil(n / kRadixBlock) + 1]
+  unsigned long long *blocksum;  // [ceil(n / kBinBlock) + 1]
   uint32_t *pkey, *pval;   // emitted pairs
   Ctrl *ctrl;
 };

@@ -179,12 +179,89 @@ __device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigne
 }
 
 // Sum of tile counts per block of kRadixBlock depth-ordered Gaussians.
-__global__ void __launch_bounds__(256) count_kernel(BinArgs a) {
-  const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+// The tiles a splat reaches: per row of tiles of its footprint box, the run of
+// tiles whose box of pixel centres meets the ellipse p <= cut', where p = A dx^2
+// + B dx dy + C dy^2 is the splat's exponent (conic with k log2 e folded in) and
+// cut' the rasteriser's cut log2(opacity / alpha_min) + 1e-3 with a further
+// 0.1 % + 0.01 of margin, so a dropped tile never holds a pixel where
+// a >= alpha_min. The ellipse cut by a band of rows is convex, so its x-extent
+// is one interval: on the right, the ellipse's rightmost point if that point's
+// y lies in the band, else the larger value of the (concave) boundary function
+// x = mx - B/(2A) dy + sqrt(cut'/A - D/(4A^2) dy^2), D = 4AC - B^2, at the
+// band's ends; the left side likewise. A tile meets the ellipse iff its
+// pixel-centre interval meets that extent.
+struct Footprint {
+  float mx, my, bx, cutA, dA, ry, rx, yr, yl;
+  unsigned x0, x1, y0, y1;  // the box, in tiles (half open)
+};
+
+__device__ __forceinline__ Footprint footprint(const BinArgs &a, uint32_t g, uint2 rc) {
+  Footprint f;
+  const float4 m = a.smean[g], k = a.sconic[g];
+  const float A = k.x, B = k.y, C = k.z;
+  const float cut = (log2f(k.w / a.alpha_min) + 1e-3f) * 1.001f + 0.01f;
+  const float D = fmaxf(4.f * A * C - B * B, 1e-30f);
+  f.mx = m.x + m.z;
+  f.my = m.y + m.w;
+  f.bx = B / (2.f * A);         // x of the centre line: mx - bx dy
+  f.cutA = cut / A;
+  f.dA = D / (4.f * A * A);
+  f.ry = sqrtf(cut * 4.f * A / D) * 1.0001f + 1e-3f;  // half extents
+  f.rx = sqrtf(cut * 4.f * C / D) * 1.0001f + 1e-3f;
+  const float by = B / (2.f * C);
+  f.yr = f.my - by * f.rx;      // y of the rightmost point
+  f.yl = f.my + by * f.rx;      // y of the leftmost point
+  f.x0 = rc.x & 0xffffu;
+  f.x1 = rc.x >> 16;
+  f.y0 = rc.y & 0xffffu;
+  f.y1 = rc.y >> 16;
+  return f;
+}
+
+// Tiles [*lo, *hi) of row ty that the ellipse reaches (within the box).
+__device__ __forceinline__ void row_span(const Footprint &f, unsigned ty, unsigned *lo,
+                                         unsigned *hi) {
+  *lo = *hi = f.x0;
+  const float ya = fmaxf((float)(ty * kTile) + 0.5f, f.my - f.ry);
+  const float yb = fminf((float)(ty * kTile) + (kTile - 0.5f), f.my + f.ry);
+  if (ya > yb) return;
+  auto hw = [&](float y) {
+    const float d = y - f.my;
+    return sqrtf(fmaxf(f.cutA - f.dA * d * d, 0.f));
+  };
+  const float ca = f.mx - f.bx * (ya - f.my), cb = f.mx - f.bx * (yb - f.my);
+  const float wa = hw(ya), wb = hw(yb);
+  const float xr = (f.yr >= ya && f.yr <= yb) ? f.mx + f.rx : fmaxf(ca + wa, cb + wb);
+  const float xl = (f.yl >= ya && f.yl <= yb) ? f.mx - f.rx : fminf(ca - wa, cb - wb);
+  // tile tx covers pixel centres [16 tx + 0.5, 16 tx + 15.5]
+  const float tl = ceilf((xl - 1e-3f - (kTile - 0.5f)) / kTile);
+  const float th = floorf((xr + 1e-3f - 0.5f) / kTile) + 1.f;
+  const float l = fmaxf(tl, (float)f.x0), h = fminf(th, (float)f.x1);
+  if (h > l) {
+    *lo = (unsigned)l;
+    *hi = (unsigned)h;
+  }
+}
+
+__device__ __forceinline__ unsigned tiles_hit(const BinArgs &a, uint32_t g, uint2 rc) {
+  const Footprint f = footprint(a, g, rc);
+  unsigned c = 0;
+  for (unsigned ty = f.y0; ty < f.y1; ++ty) {
+    unsigned lo, hi;
+    row_span(f, ty, &lo, &hi);
+    c += hi - lo;
+  }
+  return c;
+}
+
+// One Gaussian per thread (kBinBlock per block): the block's sum of tile counts.
+__global__ void __launch_bounds__(kBinBlock) count_kernel(BinArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * kBinBlock + threadIdx.x;
   unsigned long long s = 0;
-  for (int r = 0; r < kRadixItems; ++r) {
-    const int64_t i = base + r * 256 + threadIdx.x;
-    if (i < a.n) s += rect_tiles(a.rect[a.order[i]]);
+  if (i < a.n) {
+    const uint32_t g = a.order[i];
+    const uint2 rc = a.rect[g];
+    if (rect_tiles(rc)) s = tiles_hit(a, g, rc);
   }
   unsigned long long tot;
   block_exclusive_scan(s, &tot);
@@ -229,32 +306,31 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(BinArgs a, int nb) 
   }
 }
 
-__global__ void __launch_bounds__(256) emit_kernel(BinArgs a) {
-  const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
-  unsigned long long off = a.blocksum[blockIdx.x];
-  for (int r = 0; r < kRadixItems; ++r) {
-    const int64_t i = base + r * 256 + threadIdx.x;
-    const bool in = i < a.n;
-    uint32_t g = 0;
-    uint2 rc = make_uint2(0, 0);
-    if (in) {
-      g = a.order[i];
-      rc = a.rect[g];
+// Pairs of one Gaussian per thread, at the offset its block's scan gives.
+__global__ void __launch_bounds__(kBinBlock) emit_kernel(BinArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * kBinBlock + threadIdx.x;
+  const bool in = i < a.n;
+  uint32_t g = 0;
+  uint2 rc = make_uint2(0, 0);
+  if (in) {
+    g = a.order[i];
+    rc = a.rect[g];
+  }
+  const unsigned cnt = (in && rect_tiles(rc)) ? tiles_hit(a, g, rc) : 0u;
+  unsigned long long tot;
+  const unsigned long long my = a.blocksum[blockIdx.x] + block_exclusive_scan(cnt, &tot);
+  if (cnt) {
+    const Footprint f = footprint(a, g, rc);
+    unsigned long long p = my;
+    for (unsigned ty = f.y0; ty < f.y1; ++ty) {
+      unsigned lo, hi;
+      row_span(f, ty, &lo, &hi);
+      for (unsigned tx = lo; tx < hi; ++tx, ++p)
+        if (p < a.pair_cap) {
+          a.pkey[p] = ty * (unsigned)a.tiles_x + tx;
+          a.pval[p] = g;
+        }
     }
-    const unsigned cnt = in ? rect_tiles(rc) : 0u;
-    unsigned long long tot;
-    const unsigned long long my = off + block_exclusive_scan(cnt, &tot);
-    if (cnt) {
-      const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-      unsigned long long p = my;
-      for (unsigned ty = y0; ty < y1; ++ty)
-        for (unsigned tx = x0; tx < x1; ++tx, ++p)
-          if (p < a.pair_cap) {
-            a.pkey[p] = ty * (unsigned)a.tiles_x + tx;
-            a.pval[p] = g;
-          }
-    }
-    off += tot;
   }
 }
 
@@ -326,10 +402,10 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 
 cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  const int nb = (int)((a.n + kRadixBlock - 1) / kRadixBlock);
-  { LaunchScope ls_("pair_count", st); count_kernel<<<nb, 256, 0, st>>>(a); }
+  const int nb = (int)((a.n + kBinBlock - 1) / kBinBlock);
+  { LaunchScope ls_("pair_count", st); count_kernel<<<nb, kBinBlock, 0, st>>>(a); }
   { LaunchScope ls_("pair_scan", st); blocksum_scan_kernel<<<1, 1024, 0, st>>>(a, nb); }
-  { LaunchScope ls_("pair_emit", st); emit_kernel<<<nb, 256, 0, st>>>(a); }
+  { LaunchScope ls_("pair_emit", st); emit_kernel<<<nb, kBinBlock, 0, st>>>(a); }
   return cudaGetLastError();
 }
 
