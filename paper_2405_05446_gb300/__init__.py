@@ -232,10 +232,16 @@ def profile_end(max_entries: int = 64) -> dict:
 
 
 class Renderer:
-    """Owns one workspace and renders views of scenes with up to `n` Gaussians."""
+    """Owns one workspace and renders views of scenes with up to `n` Gaussians.
+
+    With graphs (the default) a view is one replay of a CUDA graph captured from
+    render_view_devcam: one graph per (Gaussian tensors, output, image size, mean),
+    captured at its first use after one ordinary render, replayed for any camera
+    (written to a device buffer first, in stream order). It runs the same kernels
+    as render_view without the gaps between launches."""
 
     def __init__(self, n: int, channels: int, width: int, height: int, ropts=None, sopts=None,
-                 device="cuda"):
+                 device="cuda", graphs: bool = True):
         import torch
         self.ropts = ropts if ropts is not None else raster_opts()
         self.sopts = sopts if sopts is not None else solver_opts()
@@ -245,12 +251,42 @@ class Renderer:
             raise ValueError("unsupported sizes or options")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.device = device
+        self.graphs = graphs
+        self._views = {}
+
+    def _view_graph(self, g: DeviceGaussians, cam, mean, out, stream):
+        import ctypes
+        import torch
+        key = (tuple(t.data_ptr() for t in (g.mean, g.scale, g.quat, g.opacity, g.grad)), g.n,
+               out.data_ptr(), cam.width, cam.height, tuple(float(m) for m in mean))
+        entry = self._views.get(key)
+        if entry is None:
+            cam_dev = torch.empty(ctypes.sizeof(_abi.Camera), dtype=torch.uint8, device=self.device)
+            cam_dev.copy_(torch.frombuffer(bytearray(camera_bytes(cam)), dtype=torch.uint8))
+            s = torch.cuda.Stream(device=out.device)
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                render_view_devcam(g, cam, cam_dev, mean, out, self.ws, self.ropts, self.sopts)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+                render_view_devcam(g, cam, cam_dev, mean, out, self.ws, self.ropts, self.sopts)
+            stream.wait_stream(s)
+            entry = self._views[key] = (graph, cam_dev)
+        return entry
 
     def render_view(self, g: DeviceGaussians, cam, mean, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
-        render_view(g, cam, mean, out, self.ws, self.ropts, self.sopts, stream)
+        if not self.graphs:
+            render_view(g, cam, mean, out, self.ws, self.ropts, self.sopts, stream)
+            return out
+        st = stream if stream is not None else torch.cuda.current_stream()
+        graph, cam_dev = self._view_graph(g, cam, mean, out, st)
+        with torch.cuda.stream(st):
+            cam_dev.copy_(torch.frombuffer(bytearray(camera_bytes(cam)), dtype=torch.uint8),
+                          non_blocking=True)
+            graph.replay()
         return out
 
     def render_gradients(self, g: DeviceGaussians, cam, maps=None, mask=None, stream=None):

@@ -372,6 +372,27 @@ def test_render_view_workspace_too_small_raises():
     assert e.value.code == G._abi.ERR_WORKSPACE
 
 
+def test_renderer_graph_replays_match_direct_renders():
+    """Renderer replays one captured graph per (Gaussians, output, size, mean) for any
+    camera: every replay equals a direct render_view of that camera bit for bit."""
+    scene, cam0 = _small_prims(n=8000)
+    g = G.gaussians_to_device(scene)
+    r = G.Renderer(scene.n, 3, cam0.width, cam0.height)
+    ws = torch.empty_like(r.ws)
+    out = torch.empty((3, cam0.height, cam0.width), device="cuda")
+    ref = torch.empty_like(out)
+    rng = np.random.default_rng(2)
+    for i in range(4):
+        cam = S.sphere_camera(rng, cam0.width, cam0.height) if i else cam0
+        r.render_view(g, cam, [0.5, 0.4, 0.6], out)
+        st = r.stats()
+        G.render_view(g, cam, [0.5, 0.4, 0.6], ref, ws)
+        st2 = G.sync_status(ws)
+        assert st["status"] == st2["status"] == 0 and st["cycles"] == st2["cycles"]
+        assert torch.equal(out, ref), i
+    assert len(r._views) == 1
+
+
 def test_graph_and_direct_cycle_loops_agree():
     """The cycle loop launched as a CUDA graph (WHILE node, default) and as direct
     launches (used while profiling) give bit-identical images and cycle counts."""
