@@ -41,6 +41,7 @@ __device__ __forceinline__ bool on_tile(const uint8_t *mask, int tiles_x, int i,
 }
 
 __global__ void __launch_bounds__(256) divergence_adjoint_kernel(DivAdjArgs a) {
+  griddep_enter();
   const size_t plane = (size_t)a.H * a.W;
   const size_t total = plane * a.C;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total;
@@ -72,6 +73,7 @@ __device__ __forceinline__ void warp_sum(float (&v)[N]) {
 
 template <int Q>
 __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
+  griddep_enter();
   __shared__ float4 s_geo[256];   // mx, my (tile-relative), A, B
   __shared__ float4 s_geo2[256];  // C, opacity, exponent limit, -
   __shared__ float s_g[Q][256];
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
 }
 
 __global__ void __launch_bounds__(256) project_backward_kernel(ProjBwdArgs a) {
+  griddep_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float *ds = a.dsplat + (size_t)i * 6;
@@ -307,7 +310,7 @@ cudaError_t launch_divergence_adjoint(const DivAdjArgs &a, cudaStream_t st) {
   const size_t total = (size_t)a.C * a.H * a.W;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 8192) blocks = 8192;
-  { LaunchScope ls_("divergence_adjoint", st); divergence_adjoint_kernel<<<blocks, 256, 0, st>>>(a); }
+  { LaunchScope ls_("divergence_adjoint", st); launch_k(divergence_adjoint_kernel, blocks, 256, 0, st, a); }
   return cudaGetLastError();
 }
 
@@ -315,12 +318,12 @@ cudaError_t launch_raster_backward(const RasterBwdArgs &a, cudaStream_t st) {
   if (a.T == 0) return cudaSuccess;
   LaunchScope ls_("raster_backward", st);
   switch (a.Q) {
-    case 1: raster_backward_kernel<1><<<a.T, 256, 0, st>>>(a); break;
-    case 2: raster_backward_kernel<2><<<a.T, 256, 0, st>>>(a); break;
-    case 3: raster_backward_kernel<3><<<a.T, 256, 0, st>>>(a); break;
-    case 4: raster_backward_kernel<4><<<a.T, 256, 0, st>>>(a); break;
-    case 6: raster_backward_kernel<6><<<a.T, 256, 0, st>>>(a); break;
-    case 8: raster_backward_kernel<8><<<a.T, 256, 0, st>>>(a); break;
+    case 1: launch_k(raster_backward_kernel<1>, a.T, 256, 0, st, a); break;
+    case 2: launch_k(raster_backward_kernel<2>, a.T, 256, 0, st, a); break;
+    case 3: launch_k(raster_backward_kernel<3>, a.T, 256, 0, st, a); break;
+    case 4: launch_k(raster_backward_kernel<4>, a.T, 256, 0, st, a); break;
+    case 6: launch_k(raster_backward_kernel<6>, a.T, 256, 0, st, a); break;
+    case 8: launch_k(raster_backward_kernel<8>, a.T, 256, 0, st, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -329,7 +332,7 @@ cudaError_t launch_raster_backward(const RasterBwdArgs &a, cudaStream_t st) {
 cudaError_t launch_project_backward(const ProjBwdArgs &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((a.n + 255) / 256);
-  { LaunchScope ls_("project_backward", st); project_backward_kernel<<<blocks, 256, 0, st>>>(a); }
+  { LaunchScope ls_("project_backward", st); launch_k(project_backward_kernel, blocks, 256, 0, st, a); }
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Diagnostics: a process-wide count of kernels this library enqueued, and an
 // opt-in per-kernel timer built from CUDA events recorded on the launching
 // stream around each launch (aggregated by kernel name when read back).
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -38,6 +39,14 @@ cudaEvent_t take_event() {
 }
 
 }  // namespace
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("GDGS_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 
 bool diag_profiling() { return g_profiling.load(std::memory_order_acquire) != 0; }
 

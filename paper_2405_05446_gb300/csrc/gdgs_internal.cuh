@@ -51,6 +51,41 @@ void diag_after(cudaStream_t st);
 bool diag_profiling();
 void diag_set_capturing(bool on);  // launches on this thread are being captured into a graph
 unsigned long long graph_kernel_count();  // kernels run by graph-launched cycle loops
+// Programmatic dependent launch. Every kernel of the library begins with
+// griddep_enter(): it waits until the kernel launched before it on the stream
+// has completed and its writes are visible (griddepcontrol.wait), and then
+// allows the next kernel to be launched (griddepcontrol.launch_dependents).
+// Kernels are launched with the programmatic-serialization attribute (below),
+// so a dependent grid is scheduled onto SMs while the last wave of its
+// predecessor drains and starts at once when that one completes, instead of
+// after a full launch round trip. The wait comes before any global access of
+// every thread, so the order of all reads and writes is that of plain stream
+// order, and a kernel completes only after its predecessor has.
+__device__ __forceinline__ void griddep_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();  // GDGS_PDL=0 turns the attribute off (diag.cu)
+
+// Launch with the programmatic-serialization attribute (when enabled). Errors
+// are reported by the caller's cudaGetLastError, as for <<<>>> launches.
+template <typename... K, typename... A>
+inline void launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<A &&>(args)...);
+}
+
 struct LaunchScope {
   cudaStream_t st;
   LaunchScope(const char *name, cudaStream_t s) : st(s) { diag_before(name, s); }

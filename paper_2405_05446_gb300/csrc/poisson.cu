@@ -787,6 +787,7 @@ __device__ __forceinline__ Rhs rhs_of(const LvArgs &a, const Ctrl *ctrl, int k, 
 // Down: nu1 sweeps on L u = f from u = 0, write u, restrict f - L u.
 template <int NU, int TY_, int TX_>
 __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctrl, int k_in, int first) {
+  griddep_enter();
   using G = Geo<NU, TY_, TX_>;
   extern __shared__ float4 sm4[];
   float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR;
@@ -815,6 +816,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
 // u_{k+1} = u_k + e (float-float), r_{k+1} = r_k - L e, ||r_{k+1}||^2, sum(u_{k+1}).
 template <int NU, int TY_, int TX_>
 __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
+  griddep_enter();
   using G = Geo<NU, TY_, TX_>;
   extern __shared__ float4 sm4[];
   float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR, *EC = U + G::ARR;
@@ -1082,6 +1084,7 @@ __device__ __forceinline__ float tail_residual(const TailLevel &t, int I, int J,
 
 __global__ void __launch_bounds__(kTailThreads)
 mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
+  griddep_enter();
   extern __shared__ float4 sm4[];
   float *S = reinterpret_cast<float *>(sm4);
   const int k = cycle_index(ctrl, k_in);
@@ -1256,6 +1259,7 @@ __device__ __forceinline__ float residual_scale(double rnorm2, long long cells) 
 __global__ void __launch_bounds__(1024)
 coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl *ctrl, int C,
                     long long npx) {
+  griddep_enter();
   __shared__ int match;
   __shared__ double fcol[260];
   const int n = g.H * g.W;
@@ -1340,6 +1344,7 @@ __device__ __forceinline__ bool tile_on(const uint8_t *mask, int tiles_x, int i,
 // with gradients of tiles whose mask is 0 read as zero (or rho read directly for
 // Laplacian fields); then the hard threshold T of Eq. thresh when t > 0; ||rho||^2.
 __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) {
+  griddep_enter();
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     ctrl->rtol = a.rtol;
     ctrl->max_cycles = a.max_cycles;
@@ -1388,6 +1393,7 @@ struct FinArgs {
 // image = u + (m_c - mean(u_c)) for the iterate the cycle loop stopped at, and
 // the residual rho - L u of that iterate in float-float arithmetic.
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
+  griddep_enter();
   const int stopped = ctrl->stopped;
   const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
   const int c = blockIdx.y;
@@ -1430,6 +1436,7 @@ __device__ unsigned long long g_graph_kernels = 0;
 // index, and (inside a graph) set the loop condition.
 __global__ void advance_kernel(Ctrl *ctrl, int k_in, cudaGraphConditionalHandle h, int in_graph,
                                unsigned kernels_per_cycle, long long cells) {
+  griddep_enter();
   const int k = k_in >= 0 ? k_in : ctrl->iter;
   if (k + 1 <= kMaxCycles) ctrl->escale[k + 1] = residual_scale(ctrl->rnorm2[k + 1], cells);
   if (!ctrl->stopped) {
@@ -1485,7 +1492,7 @@ cudaError_t launch_mg_down_t(const LvArgs &a, Ctrl *ctrl, int k, int first, int 
   const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
   {
     LaunchScope ls_(a.level0 ? "mg0_down" : "mg_down", st);
-    mg_down_kernel<NU, TY_, TX_><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k, first);
+    launch_k(mg_down_kernel<NU, TY_, TX_>, grid, dim3(kBX, kBY), sm, st, a, ctrl, k, first);
   }
   return cudaGetLastError();
 }
@@ -1499,7 +1506,7 @@ cudaError_t launch_mg_up_t(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream
   const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
   {
     LaunchScope ls_(a.level0 ? "mg0_up" : "mg_up", st);
-    mg_up_kernel<NU, TY_, TX_><<<grid, dim3(kBX, kBY), sm, st>>>(a, ctrl, k);
+    launch_k(mg_up_kernel<NU, TY_, TX_>, grid, dim3(kBX, kBY), sm, st, a, ctrl, k);
   }
   return cudaGetLastError();
 }
@@ -1620,7 +1627,7 @@ struct Cycle {
     }
     {
       LaunchScope ls_("mg_tail", st);
-      mg_tail_kernel<<<C, kTailThreads, tail_smem(*p, t), st>>>(tail(), ctrl, k, t == 1 ? 1 : 0);
+      launch_k(mg_tail_kernel, C, kTailThreads, tail_smem(*p, t), st, tail(), ctrl, k, t == 1 ? 1 : 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     for (int l = t - 1; l >= 0; --l) {
@@ -1632,7 +1639,7 @@ struct Cycle {
     }
     {
       LaunchScope ls_("mg_advance", st);
-      advance_kernel<<<1, 1, 0, st>>>(ctrl, k, h, in_graph, kernels(),
+      launch_k(advance_kernel, 1, 1, 0, st, ctrl, k, h, in_graph, kernels(),
                                       (long long)C * p->lv[0].plane);
     }
     return cudaGetLastError();
@@ -1805,7 +1812,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
     const size_t plane = (size_t)a.H * a.W;
     int bx = (int)((plane + 255) / 256);
     if (bx > 4096) bx = 4096;
-    { LaunchScope ls_("divergence", st); divergence_kernel<<<dim3(bx, a.C), 256, 0, st>>>(d, ctrl); }
+    { LaunchScope ls_("divergence", st); launch_k(divergence_kernel, dim3(bx, a.C), 256, 0, st, d, ctrl); }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
@@ -1824,7 +1831,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   double *Minv = (double *)(ws + p.off_coarse + kCoarseTagBytes);
   {
     LaunchScope ls_("coarse_setup", st);
-    coarse_setup_kernel<<<1, 1024, 0, st>>>(gcoarse, Minv, tag, want, ctrl, a.C,
+    launch_k(coarse_setup_kernel, 1, 1024, 0, st, gcoarse, Minv, tag, want, ctrl, a.C,
                                             (long long)a.H * a.W);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1870,7 +1877,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
     const size_t plane = (size_t)a.H * a.W;
     int bx = (int)((plane + 255) / 256);
     if (bx > 2048) bx = 2048;
-    { LaunchScope ls_("finalize", st); finalize_kernel<<<dim3(bx, a.C), 256, 0, st>>>(fa, ctrl); }
+    { LaunchScope ls_("finalize", st); launch_k(finalize_kernel, dim3(bx, a.C), 256, 0, st, fa, ctrl); }
   }
   return cudaGetLastError();
 }

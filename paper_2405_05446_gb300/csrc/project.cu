@@ -24,6 +24,7 @@ namespace gdgs {
 namespace {
 
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
+  griddep_enter();
   if (a.cam_dev) {  // camera from device memory (a graph replays for any camera)
     const gdgs_camera *cd = a.cam_dev;
 #pragma unroll
@@ -166,7 +167,7 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-  { LaunchScope ls_("project", st); project_kernel<<<blocks, threads, 0, st>>>(a); }
+  { LaunchScope ls_("project", st); launch_k(project_kernel, blocks, threads, 0, st, a); }
   return cudaGetLastError();
 }
 

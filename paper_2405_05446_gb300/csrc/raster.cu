@@ -28,6 +28,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 template <int Q>
 __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
+  griddep_enter();
   constexpr int QV = (Q + 3) / 4;  // float4 slots of the gradient attribute
   // splat batch, packed so that one pixel-splat evaluation reads 2 broadcast
   // 16-byte words (plus QV more when the splat contributes)
@@ -112,12 +113,12 @@ cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st) {
   if (a.T == 0) return cudaSuccess;
   LaunchScope ls_("raster", st);
   switch (a.Q) {
-    case 1: raster_kernel<1><<<a.T, 256, 0, st>>>(a); break;
-    case 2: raster_kernel<2><<<a.T, 256, 0, st>>>(a); break;
-    case 3: raster_kernel<3><<<a.T, 256, 0, st>>>(a); break;
-    case 4: raster_kernel<4><<<a.T, 256, 0, st>>>(a); break;
-    case 6: raster_kernel<6><<<a.T, 256, 0, st>>>(a); break;
-    case 8: raster_kernel<8><<<a.T, 256, 0, st>>>(a); break;
+    case 1: launch_k(raster_kernel<1>, a.T, 256, 0, st, a); break;
+    case 2: launch_k(raster_kernel<2>, a.T, 256, 0, st, a); break;
+    case 3: launch_k(raster_kernel<3>, a.T, 256, 0, st, a); break;
+    case 4: launch_k(raster_kernel<4>, a.T, 256, 0, st, a); break;
+    case 6: launch_k(raster_kernel<6>, a.T, 256, 0, st, a); break;
+    case 8: launch_k(raster_kernel<8>, a.T, 256, 0, st, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

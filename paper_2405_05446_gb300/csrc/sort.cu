@@ -36,6 +36,7 @@ __device__ __forceinline__ unsigned item_count(const unsigned long long *n_dev, 
 __global__ void __launch_bounds__(kRadixThreads)
 radix_hist_kernel(const uint32_t *keys, const unsigned long long *n_dev, unsigned cap,
                   int shift, unsigned mask, uint32_t *hist) {
+  griddep_enter();
   __shared__ unsigned sh[256];
   const unsigned n = item_count(n_dev, cap);
   const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
@@ -79,6 +80,7 @@ __device__ __forceinline__ unsigned scan256(unsigned v, unsigned *total) {
 // in place; the digit's total goes to tot[d].
 __global__ void __launch_bounds__(256)
 radix_scan_digit_kernel(uint32_t *hist, uint32_t *tot, const unsigned long long *n_dev, unsigned cap) {
+  griddep_enter();
   const unsigned n = item_count(n_dev, cap);
   const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
   uint32_t *h = hist + (size_t)blockIdx.x * nb;
@@ -96,6 +98,7 @@ radix_scan_digit_kernel(uint32_t *hist, uint32_t *tot, const unsigned long long 
 
 // Exclusive scan of the digit totals into the digit bases (in place).
 __global__ void __launch_bounds__(256) radix_scan_top_kernel(uint32_t *tot, unsigned ndig) {
+  griddep_enter();
   const unsigned v = threadIdx.x < ndig ? tot[threadIdx.x] : 0u;
   unsigned t;
   const unsigned ex = scan256(v, &t);
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                      uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
                      unsigned mask, const uint32_t *hist, const uint32_t *dbase) {
+  griddep_enter();
   constexpr int kWarps = kRadixThreads / 32;
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kWarps][256];
@@ -256,6 +260,7 @@ __device__ __forceinline__ unsigned tiles_hit(const BinArgs &a, uint32_t g, uint
 
 // One Gaussian per thread (kBinBlock per block): the block's sum of tile counts.
 __global__ void __launch_bounds__(kBinBlock) count_kernel(BinArgs a) {
+  griddep_enter();
   const int64_t i = (int64_t)blockIdx.x * kBinBlock + threadIdx.x;
   unsigned long long s = 0;
   if (i < a.n) {
@@ -269,6 +274,7 @@ __global__ void __launch_bounds__(kBinBlock) count_kernel(BinArgs a) {
 }
 
 __global__ void __launch_bounds__(1024) blocksum_scan_kernel(BinArgs a, int nb) {
+  griddep_enter();
   __shared__ unsigned long long wt[32];
   const int per = (nb + 1023) / 1024;
   const int b = threadIdx.x * per, e = min(b + per, nb);
@@ -308,6 +314,7 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(BinArgs a, int nb) 
 
 // Pairs of one Gaussian per thread, at the offset its block's scan gives.
 __global__ void __launch_bounds__(kBinBlock) emit_kernel(BinArgs a) {
+  griddep_enter();
   const int64_t i = (int64_t)blockIdx.x * kBinBlock + threadIdx.x;
   const bool in = i < a.n;
   uint32_t g = 0;
@@ -339,6 +346,7 @@ __global__ void __launch_bounds__(kBinBlock) emit_kernel(BinArgs a) {
 __global__ void __launch_bounds__(256)
 ranges_kernel(const uint32_t *keys, Ctrl *ctrl, unsigned cap, int T, uint2 *range,
               uint32_t *active, uint8_t *mask) {
+  griddep_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned long long np = ctrl->n_pairs;
   const unsigned n = np < cap ? (unsigned)np : cap;
@@ -382,13 +390,13 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const int bits = nbits - shift < 8 ? nbits - shift : 8;
     const unsigned mask = (1u << bits) - 1u;
     if (blocks == 0) break;
-    { LaunchScope ls_("radix_hist", st); radix_hist_kernel<<<blocks, kRadixThreads, 0, st>>>(ki, n_dev, cap, shift, mask, hist); }
+    { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
     uint32_t *dtot = hist + (size_t)256 * max_blocks;
-    { LaunchScope ls_("radix_scan", st); radix_scan_digit_kernel<<<mask + 1, 256, 0, st>>>(hist, dtot, n_dev, cap); }
-    { LaunchScope ls_("radix_scan_top", st); radix_scan_top_kernel<<<1, 256, 0, st>>>(dtot, mask + 1); }
+    { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
+    { LaunchScope ls_("radix_scan_top", st); launch_k(radix_scan_top_kernel, 1, 256, 0, st, dtot, mask + 1); }
     {
       LaunchScope ls_("radix_scatter", st);
-      radix_scatter_kernel<<<blocks, kRadixThreads, 0, st>>>(
+      launch_k(radix_scatter_kernel, blocks, kRadixThreads, 0, st,
           ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist, dtot);
     }
     first = false;
@@ -403,16 +411,16 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   const int nb = (int)((a.n + kBinBlock - 1) / kBinBlock);
-  { LaunchScope ls_("pair_count", st); count_kernel<<<nb, kBinBlock, 0, st>>>(a); }
-  { LaunchScope ls_("pair_scan", st); blocksum_scan_kernel<<<1, 1024, 0, st>>>(a, nb); }
-  { LaunchScope ls_("pair_emit", st); emit_kernel<<<nb, kBinBlock, 0, st>>>(a); }
+  { LaunchScope ls_("pair_count", st); launch_k(count_kernel, nb, kBinBlock, 0, st, a); }
+  { LaunchScope ls_("pair_scan", st); launch_k(blocksum_scan_kernel, 1, 1024, 0, st, a, nb); }
+  { LaunchScope ls_("pair_emit", st); launch_k(emit_kernel, nb, kBinBlock, 0, st, a); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges(const uint32_t *sorted_keys, Ctrl *ctrl, unsigned pair_cap,
                                int T, uint2 *range, uint32_t *active, uint8_t *mask,
                                cudaStream_t st) {
-  { LaunchScope ls_("tile_ranges", st); ranges_kernel<<<(T + 255) / 256, 256, 0, st>>>(sorted_keys, ctrl, pair_cap, T, range, active, mask); }
+  { LaunchScope ls_("tile_ranges", st); launch_k(ranges_kernel, (T + 255) / 256, 256, 0, st, sorted_keys, ctrl, pair_cap, T, range, active, mask); }
   return cudaGetLastError();
 }
 
