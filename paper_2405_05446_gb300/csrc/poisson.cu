@@ -935,11 +935,18 @@ __host__ __device__ __forceinline__ int tail_stride(const LevelGeom &g) {
 // Shared-memory layout of the tail: u and f of every level, then per level the
 // row tables (H entries each: wy, cS, cN, and the prolongation rows i0, i1, w
 // from the next coarser level) and the column tables (W entries each: wx, cE,
-// cW, i0, i1, w), then (for small coarsest grids) the FP64 inverse. A cell's
-// face coefficients are products of one row and one column factor (e = wy cE,
-// w = wy cW, s = wx cS, n = wx cN), so every sweep, residual and prolongation
-// is branch-free. Offsets are computed on the host.
+// cW, i0, i1, w), then -f of the coarsest level and the partial sums of its
+// product in FP64, then (for small coarsest grids) the FP64 inverse, stored
+// transposed. A cell's face coefficients are products of one row and one
+// column factor (e = wy cE, w = wy cW, s = wx cS, n = wx cN), so every sweep,
+// residual and prolongation is branch-free. Offsets are computed on the host.
 constexpr int kTailMinvStage = 64;  // stage the inverse when nc <= this
+
+// Threads per row of the coarse solve's product (nc <= 1024 cells).
+__host__ __device__ __forceinline__ int tail_parts(int nc) {
+  const int p = kTailThreads / (nc > 0 ? nc : 1);
+  return p < 1 ? 1 : (p > 8 ? 8 : p);
+}
 
 inline size_t tail_layout(const LevelGeom *lv, int n, TailArgs *a) {
   size_t o = 0;
@@ -954,7 +961,7 @@ inline size_t tail_layout(const LevelGeom *lv, int n, TailArgs *a) {
   const long long nc = lv[n - 1].plane;
   o = (o + 1) & ~(size_t)1;  // 8-byte alignment for the doubles
   if (a) a->off_fd = (int)o;
-  o += 2 * (size_t)nc;
+  o += 2 * (size_t)nc * (1 + tail_parts((int)nc));  // -f, then the partial sums
   if (nc <= kTailMinvStage) {
     if (a) a->off_minv = (int)o;
     o += 2 * (size_t)(nc * nc);
@@ -1123,7 +1130,10 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int q = q0 + j * kTailThreads;
-          if (q < n2) M[q] = v[j];
+          if (q < n2) {
+            const int row = q / nc;
+            M[(q - row * nc) * nc + row] = v[j];
+          }
         }
       }
     }
@@ -1155,25 +1165,36 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
     }
     __syncthreads();
   }
-  {  // coarsest: u = Minv (-f) in FP64; one thread per row, four partial sums
+  {  // coarsest: u = Minv (-f) in FP64. FP64 issues slowly, so the products are
+     // spread over P threads per row, each a run of columns (read from the
+     // transposed staged inverse: consecutive rows are consecutive words), and
+     // one thread per row adds the P partial sums in order.
     const TailLevel t = tail_level_at(S, a, a.n - 1);
-    const int nc = t.H * t.W;
-    const double *M = a.off_minv >= 0 ? reinterpret_cast<const double *>(S + a.off_minv) : a.Minv;
-    double *fd = reinterpret_cast<double *>(S + a.off_fd);
+    const int nc = t.H * t.W, P = tail_parts(nc), len = (nc + P - 1) / P;
+    const bool staged = a.off_minv >= 0;
+    const double *M = staged ? reinterpret_cast<const double *>(S + a.off_minv) : a.Minv;
+    const size_t rs = staged ? 1 : (size_t)nc, cs = staged ? (size_t)nc : 1;  // (row, j) at row rs + j cs
+    double *fd = reinterpret_cast<double *>(S + a.off_fd), *part = fd + nc;
     for (int j = tid; j < nc; j += kTailThreads) fd[j] = -(double)t.f[j];
     __syncthreads();
-    for (int row = tid; row < nc; row += kTailThreads) {
-      const double *mr = M + (size_t)row * nc;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int j = 0;
-      for (; j + 3 < nc; j += 4) {
-        s0 = fma(mr[j], fd[j], s0);
-        s1 = fma(mr[j + 1], fd[j + 1], s1);
-        s2 = fma(mr[j + 2], fd[j + 2], s2);
-        s3 = fma(mr[j + 3], fd[j + 3], s3);
+    for (int w = tid; w < P * nc; w += kTailThreads) {
+      const int p = w / nc, row = w - p * nc;
+      const int j1 = min(nc, (p + 1) * len);
+      const double *mr = M + (size_t)row * rs;
+      double s0 = 0.0, s1 = 0.0;
+      int j = p * len;
+      for (; j + 1 < j1; j += 2) {
+        s0 = fma(mr[j * cs], fd[j], s0);
+        s1 = fma(mr[(j + 1) * cs], fd[j + 1], s1);
       }
-      for (; j < nc; ++j) s0 = fma(mr[j], fd[j], s0);
-      t.u[row] = (float)((s0 + s1) + (s2 + s3));
+      if (j < j1) s0 = fma(mr[j * cs], fd[j], s0);
+      part[w] = s0 + s1;
+    }
+    __syncthreads();
+    for (int row = tid; row < nc; row += kTailThreads) {
+      double s = 0.0;
+      for (int p = 0; p < P; ++p) s += part[p * nc + row];
+      t.u[row] = (float)s;
     }
     __syncthreads();
   }
