@@ -48,6 +48,7 @@
 // with a WHILE node: no launch is spent after convergence.
 #include <stdlib.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -219,6 +220,15 @@ __device__ __forceinline__ bool should_stop(Ctrl *ctrl, int k, int first) {
     return true;
   }
   return false;
+}
+
+// should_stop evaluated once per block (its FP64 products are slow here) and
+// shared; the result is uniform over the block.
+__device__ __forceinline__ bool block_should_stop(Ctrl *ctrl, int k, int first) {
+  __shared__ int s_stop;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_stop = should_stop(ctrl, k, first) ? 1 : 0;
+  __syncthreads();
+  return s_stop != 0;
 }
 
 // Block-wide sum; the result is valid in the first thread of the block.
@@ -793,7 +803,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR;
   Factors<G> *fa = reinterpret_cast<Factors<G> *>(U + G::ARR);
   const int k = cycle_index(ctrl, k_in);
-  if (a.level0 ? *(volatile int *)&ctrl->stopped != 0 : should_stop(ctrl, k, first)) return;
+  if (a.level0 ? *(volatile int *)&ctrl->stopped != 0 : block_should_stop(ctrl, k, first)) return;
   const LevelGeom &g = a.g;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
@@ -822,7 +832,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
   float *F = reinterpret_cast<float *>(sm4), *U = F + G::ARR, *EC = U + G::ARR;
   Factors<G> *fa = reinterpret_cast<Factors<G> *>(EC + G::CRY * G::CRX + (4 - (G::CRY * G::CRX) % 4) % 4);
   const int k = cycle_index(ctrl, k_in);
-  if (should_stop(ctrl, k, 0)) return;
+  if (block_should_stop(ctrl, k, 0)) return;
   const LevelGeom &g = a.g;
   const int c = blockIdx.z;
   const int ty0 = blockIdx.y * G::TY, tx0 = blockIdx.x * G::TX;
@@ -1095,7 +1105,7 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
   extern __shared__ float4 sm4[];
   float *S = reinterpret_cast<float *>(sm4);
   const int k = cycle_index(ctrl, k_in);
-  if (should_stop(ctrl, k, first)) return;
+  if (block_should_stop(ctrl, k, first)) return;
   const int c = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int kWarps = kTailThreads / 32;
@@ -1404,12 +1414,98 @@ __global__ void __launch_bounds__(256) divergence_kernel(DivArgs a, Ctrl *ctrl) 
   }
 }
 
+// The same divergence on four pixels of one row per thread (W % 4 == 0 and
+// 16-byte aligned planes): 16-byte loads and stores, one 32-bit division per
+// four pixels. A quad lies in one 16-pixel tile; only its left neighbour and
+// the row above can sit in other tiles. Each pixel's terms are added in the
+// order of the scalar kernel, so rho is bit-identical to it.
+__device__ __forceinline__ float4 ld_f4(const float *p) {
+  return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+__global__ void __launch_bounds__(256) divergence4_kernel(DivArgs a, Ctrl *ctrl) {
+  griddep_enter();
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    ctrl->rtol = a.rtol;
+    ctrl->max_cycles = a.max_cycles;
+    ctrl->channels = a.C;
+  }
+  const int c = blockIdx.y, W = a.W, H = a.H, Wq = W >> 2, nq = H * Wq;
+  const size_t plane = (size_t)H * W;
+  const float *gxp = a.maps + (size_t)(a.input_is_rho ? c : 2 * c) * plane;
+  const float *gyp = gxp + plane;
+  float *rp = a.rho + (size_t)c * plane;
+  bool bad = false;
+  float n2 = 0.f, s1 = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int i = q / Wq, j0 = (q - i * Wq) << 2;
+    const size_t p = (size_t)i * W + j0;
+    const bool on = tile_on(a.mask, a.tiles_x, i, j0);
+    float r[4];
+    if (a.input_is_rho) {
+      const float4 v = on ? ld_f4(gxp + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+      r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 gx = on ? ld_f4(gxp + p) : z;
+      const float4 gy = on && i + 1 < H ? ld_f4(gyp + p) : z;
+      const float4 gu = i >= 1 && tile_on(a.mask, a.tiles_x, i - 1, j0) ? ld_f4(gyp + p - W) : z;
+      const float gl = j0 >= 1 && tile_on(a.mask, a.tiles_x, i, j0 - 1) ? gxp[p - 1] : 0.f;
+      const float x[4] = {gx.x, gx.y, gx.z, gx.w}, y[4] = {gy.x, gy.y, gy.z, gy.w};
+      const float u[4] = {gu.x, gu.y, gu.z, gu.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float v = 0.f;
+        v += j0 + k + 1 < W ? x[k] : 0.f;
+        v -= k > 0 ? x[k - 1] : gl;
+        v += y[k];
+        v -= u[k];
+        r[k] = v;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bad |= !isfinite(r[k]);
+      if (a.threshold > 0.f && !(fabsf(r[k]) >= a.threshold)) r[k] = 0.f;
+      n2 = fmaf(r[k], r[k], n2);
+      s1 += r[k];
+    }
+    *reinterpret_cast<float4 *>(rp + p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(ctrl, GDGS_ERR_NONFINITE);
+  n2 = block_sum(n2);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctrl->rho_sq[c], (double)n2);
+    atomicAdd(&ctrl->rho_sum[c], (double)s1);
+  }
+}
+
 struct FinArgs {
   LevelGeom g0;
   const float *rho, *uhi, *ulo;
   float *image;
   float mean[GDGS_MAX_CHANNELS];
 };
+
+// m_c - mean(u_c), evaluated by one thread of the block (FP64 issues slowly on
+// this GPU, so per-thread FP64 divides would dominate the kernel).
+__device__ __forceinline__ float block_shift(float m, double sum_u, size_t plane) {
+  __shared__ float s_shift;
+  if (threadIdx.x == 0) s_shift = (float)((double)m - sum_u / (double)plane);
+  __syncthreads();
+  return s_shift;
+}
+
+// The supplied mean of channel c (a select over the parameter array, so the
+// array is not copied to local memory for a dynamic index).
+__device__ __forceinline__ float channel_mean(const float (&mean)[GDGS_MAX_CHANNELS], int c) {
+  float m = mean[0];
+#pragma unroll
+  for (int i = 1; i < GDGS_MAX_CHANNELS; ++i)
+    if (i == c) m = mean[i];
+  return m;
+}
 
 // image = u + (m_c - mean(u_c)) for the iterate the cycle loop stopped at, and
 // the residual rho - L u of that iterate in float-float arithmetic.
@@ -1420,7 +1516,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   const int c = blockIdx.y;
   const LevelGeom &g = a.g0;
   const size_t plane = (size_t)g.H * g.W;
-  const float shift = (float)((double)a.mean[c] - ctrl->sum_u[kf][c] / (double)plane);
+  const float mc = channel_mean(a.mean, c);
+  const float shift = block_shift(mc, ctrl->sum_u[kf][c], plane);
   const size_t cb = (size_t)c * plane;
   const float *uh = a.uhi + cb, *ul = a.ulo + cb;
   float r2 = 0.f;
@@ -1445,7 +1542,72 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   r2 = block_sum(r2);
   if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctrl->mean_set[c] = a.mean[c];
+    ctrl->mean_set[c] = mc;
+    if (c == 0 && !stopped) ctrl->cycles = kf;
+  }
+}
+
+// L u of one pixel in float-float parts (sh + sl), neighbours east, west,
+// south, north in that order, as in finalize_kernel.
+__device__ __forceinline__ float fin_px(float h, float l, float eh, float el, float wh, float wl,
+                                        float sh_, float sl_, float nh, float nl, bool E, bool Wst,
+                                        bool S_, bool N_) {
+  float sh = 0.f, sl = 0.f;
+  if (E) { sh += eh - h; sl += el - l; }
+  if (Wst) { sh += wh - h; sl += wl - l; }
+  if (S_) { sh += sh_ - h; sl += sl_ - l; }
+  if (N_) { sh += nh - h; sl += nl - l; }
+  return sh + sl;
+}
+
+// The same finalisation on four pixels of one row per thread (W % 4 == 0,
+// 16-byte aligned planes); per pixel the same operations in the same order as
+// the scalar kernel.
+__global__ void __launch_bounds__(256) finalize4_kernel(FinArgs a, Ctrl *ctrl) {
+  griddep_enter();
+  const int stopped = ctrl->stopped;
+  const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
+  const int c = blockIdx.y;
+  const LevelGeom &g = a.g0;
+  const int W = g.W, H = g.H, Wq = W >> 2, nq = H * Wq;
+  const size_t plane = (size_t)H * W;
+  const float mc = channel_mean(a.mean, c);
+  const float shift = block_shift(mc, ctrl->sum_u[kf][c], plane);
+  const float rm = ctrl->rho_mean[c];
+  const size_t cb = (size_t)c * plane;
+  const float *uh = a.uhi + cb, *ul = a.ulo + cb;
+  float r2 = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int i = q / Wq, j0 = (q - i * Wq) << 2;
+    const size_t p = (size_t)i * W + j0;
+    const float4 rv = ld_f4(a.rho + cb + p);
+    float r[4] = {rv.x - rm, rv.y - rm, rv.z - rm, rv.w - rm};
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    if (kf > 0) {
+      const float4 h4 = ld_f4(uh + p), l4 = ld_f4(ul + p);
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 hs = i + 1 < H ? ld_f4(uh + p + W) : z, ls = i + 1 < H ? ld_f4(ul + p + W) : z;
+      const float4 hn = i > 0 ? ld_f4(uh + p - W) : z, ln = i > 0 ? ld_f4(ul + p - W) : z;
+      const float hw = j0 > 0 ? uh[p - 1] : 0.f, lw = j0 > 0 ? ul[p - 1] : 0.f;
+      const float he = j0 + 4 < W ? uh[p + 4] : 0.f, le = j0 + 4 < W ? ul[p + 4] : 0.f;
+      const bool s_ = i + 1 < H, n_ = i > 0, w_ = j0 > 0, e_ = j0 + 4 < W;
+      r[0] -= fin_px(h4.x, l4.x, h4.y, l4.y, hw, lw, hs.x, ls.x, hn.x, ln.x, true, w_, s_, n_);
+      r[1] -= fin_px(h4.y, l4.y, h4.z, l4.z, h4.x, l4.x, hs.y, ls.y, hn.y, ln.y, true, true, s_, n_);
+      r[2] -= fin_px(h4.z, l4.z, h4.w, l4.w, h4.y, l4.y, hs.z, ls.z, hn.z, ln.z, true, true, s_, n_);
+      r[3] -= fin_px(h4.w, l4.w, he, le, h4.z, l4.z, hs.w, ls.w, hn.w, ln.w, e_, true, s_, n_);
+      hi[0] = h4.x; hi[1] = h4.y; hi[2] = h4.z; hi[3] = h4.w;
+      lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w;
+    }
+    *reinterpret_cast<float4 *>(a.image + cb + p) =
+        make_float4(hi[0] + (lo[0] + shift), hi[1] + (lo[1] + shift), hi[2] + (lo[2] + shift),
+                    hi[3] + (lo[3] + shift));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r2 = fmaf(r[k], r[k], r2);
+  }
+  r2 = block_sum(r2);
+  if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->mean_set[c] = mc;
     if (c == 0 && !stopped) ctrl->cycles = kf;
   }
 }
@@ -1818,6 +1980,11 @@ unsigned long long graph_kernel_count() {
   return v;
 }
 
+// Four-pixel kernels: rows of a multiple of 4 floats and 16-byte aligned planes.
+inline bool quad_path(int W, const void *p0, const void *p1) {
+  return W % 4 == 0 && ((uintptr_t)p0 % 16) == 0 && ((uintptr_t)p1 % 16) == 0;
+}
+
 cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   const Plan &p = *a.plan;
   char *ws = a.ws;
@@ -1831,9 +1998,16 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
             a.max_cycles};
   {
     const size_t plane = (size_t)a.H * a.W;
-    int bx = (int)((plane + 255) / 256);
-    if (bx > 4096) bx = 4096;
-    { LaunchScope ls_("divergence", st); launch_k(divergence_kernel, dim3(bx, a.C), 256, 0, st, d, ctrl); }
+    if (quad_path(a.W, a.maps, rho)) {
+      const int bx = (int)std::min<size_t>((plane / 4 + 255) / 256, 8192);
+      LaunchScope ls_("divergence", st);
+      launch_k(divergence4_kernel, dim3(bx, a.C), 256, 0, st, d, ctrl);
+    } else {
+      int bx = (int)((plane + 255) / 256);
+      if (bx > 4096) bx = 4096;
+      LaunchScope ls_("divergence", st);
+      launch_k(divergence_kernel, dim3(bx, a.C), 256, 0, st, d, ctrl);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
@@ -1896,9 +2070,16 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   for (int c = 0; c < GDGS_MAX_CHANNELS; ++c) fa.mean[c] = a.mean[c];
   {
     const size_t plane = (size_t)a.H * a.W;
-    int bx = (int)((plane + 255) / 256);
-    if (bx > 2048) bx = 2048;
-    { LaunchScope ls_("finalize", st); launch_k(finalize_kernel, dim3(bx, a.C), 256, 0, st, fa, ctrl); }
+    if (quad_path(a.W, a.image, rho)) {
+      const int bx = (int)std::min<size_t>((plane / 4 + 255) / 256, 8192);
+      LaunchScope ls_("finalize", st);
+      launch_k(finalize4_kernel, dim3(bx, a.C), 256, 0, st, fa, ctrl);
+    } else {
+      int bx = (int)((plane + 255) / 256);
+      if (bx > 2048) bx = 2048;
+      LaunchScope ls_("finalize", st);
+      launch_k(finalize_kernel, dim3(bx, a.C), 256, 0, st, fa, ctrl);
+    }
   }
   return cudaGetLastError();
 }
