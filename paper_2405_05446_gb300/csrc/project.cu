@@ -9,8 +9,8 @@
 // relative 1e-4 plus 1e-3 px so binning never drops a pixel the composite uses;
 // and the 16x16 tile rectangle it covers.
 //
-// Precision: the camera transform and the projected centre are computed in FP64
-// and stored as a (hi, lo) float pair. In FP32 the centre of a splat 1000 px from
+// Precision: the camera transform and the projected centre are computed in
+// float-float arithmetic (about 44 bits) and stored as a (hi, lo) float pair. In FP32 the centre of a splat 1000 px from
 // the origin carries ~1e-4 px of rounding, which moves alpha by ~1e-4 relative;
 // the pair keeps the later per-pixel offset accurate to FP32 relative precision.
 // The view-depth sort key is the FP32 value fma(w20, x, fma(w21, y, fma(w22, z,
@@ -22,6 +22,51 @@
 namespace gdgs {
 
 namespace {
+
+// Float-float numbers (value = hi + lo, |lo| <= ulp(hi) / 2) from error-free
+// transformations: Knuth's TwoSum and the exact product by FMA. The _rn
+// intrinsics keep the compiler from contracting or reassociating them. About
+// 44 bits of precision, with FP32 instructions only (FP64 issues slowly here).
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF ff_fast_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi), t = ff_two_sum(x.lo, y.lo);
+  const FF u = ff_fast_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return ff_fast_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+
+__device__ __forceinline__ FF ff_mul(FF x, float y) {
+  const FF p = ff_prod(x.hi, y);
+  return ff_fast_sum(p.hi, __fmaf_rn(x.lo, y, p.lo));
+}
+
+__device__ __forceinline__ FF ff_div(FF x, FF y) {
+  const float q1 = __fdiv_rn(x.hi, y.hi);
+  const FF r = ff_add(x, ff_mul({-y.hi, -y.lo}, q1));
+  return ff_fast_sum(q1, __fdiv_rn(r.hi, y.hi));
+}
+
+// w[0] x + w[1] y + w[2] z + w[3] as a float-float.
+__device__ __forceinline__ FF ff_affine(const float *w, float x, float y, float z) {
+  return ff_add(ff_add(ff_prod(w[0], x), ff_prod(w[1], y)), ff_add(ff_prod(w[2], z), FF{w[3], 0.f}));
+}
 
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   griddep_enter();
@@ -76,21 +121,17 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
       const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
       const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
 
-      // camera-space centre and projected centre in FP64
-      const double dx = mx, dy = my, dz = mz;
-      const double t0 = fma((double)a.w2c[0], dx, fma((double)a.w2c[1], dy, fma((double)a.w2c[2], dz, (double)a.w2c[3])));
-      const double t1 = fma((double)a.w2c[4], dx, fma((double)a.w2c[5], dy, fma((double)a.w2c[6], dz, (double)a.w2c[7])));
-      const double t2 = fma((double)a.w2c[8], dx, fma((double)a.w2c[9], dy, fma((double)a.w2c[10], dz, (double)a.w2c[11])));
-      const double iz = 1.0 / t2;
-      const double u = fma((double)a.fx * t0, iz, (double)a.cx);
-      const double v = fma((double)a.fy * t1, iz, (double)a.cy);
-      const float u_hi = (float)u, v_hi = (float)v;
-      const float u_lo = (float)(u - (double)u_hi), v_lo = (float)(v - (double)v_hi);
+      // camera-space centre and projected centre in float-float
+      const FF t0 = ff_affine(a.w2c, mx, my, mz), t1 = ff_affine(a.w2c + 4, mx, my, mz);
+      const FF t2 = ff_affine(a.w2c + 8, mx, my, mz);
+      const FF u = ff_add(ff_mul(ff_div(t0, t2), a.fx), FF{a.cx, 0.f});
+      const FF v = ff_add(ff_mul(ff_div(t1, t2), a.fy), FF{a.cy, 0.f});
+      const float u_hi = u.hi, v_hi = v.hi, u_lo = u.lo, v_lo = v.lo;
       u_f = u_hi;
       v_f = v_hi;
 
       // J (2x3) at t, T = J W (2x3)
-      const float tx = (float)t0, ty = (float)t1, tz = (float)t2;
+      const float tx = t0.hi, ty = t1.hi, tz = t2.hi;
       const float izf = 1.0f / tz;
       const float J00 = a.fx * izf, J02 = -a.fx * tx * izf * izf;
       const float J11 = a.fy * izf, J12 = -a.fy * ty * izf * izf;
