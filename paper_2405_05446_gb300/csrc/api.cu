@@ -74,8 +74,9 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
   const int64_t cap = n * (int64_t)ro.pairs_per_gaussian;
   if (cap > 0x7fffffffll) return false;
   p->pair_cap = (unsigned)cap;
-  const int64_t maxitems = n > cap ? n : cap;
-  p->radix_blocks_max = (int)((maxitems + kRadixBlock - 1) / kRadixBlock);
+  const int64_t dblk = (n + kRadixBlockSmall - 1) / kRadixBlockSmall;  // depth sort
+  const int64_t pblk = (cap + kRadixBlock - 1) / kRadixBlock;           // pair sort
+  p->radix_blocks_max = (int)(dblk > pblk ? dblk : pblk);
 
   // multigrid levels: coarsen until both sides <= coarse_max_dim, at least 2 levels
   int levels = 1;
@@ -235,9 +236,10 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
     // 1. depth order of the Gaussians (32-bit keys)
     uint32_t *dk0 = (uint32_t *)(ws + p.off_dkey[0]), *dv0 = (uint32_t *)(ws + p.off_dval[0]);
     uint32_t *dk1 = (uint32_t *)(ws + p.off_dkey[1]), *dv1 = (uint32_t *)(ws + p.off_dval[1]);
-    const int dblocks = (int)((g->n + kRadixBlock - 1) / kRadixBlock);
+    const int dblocks = (int)((g->n + kRadixBlockSmall - 1) / kRadixBlockSmall);
     bool alt = false;
-    e = radix_sort_pairs(dk0, dv0, dk1, dv1, true, nullptr, (unsigned)g->n, 32, hist, dblocks, &alt, st);
+    e = radix_sort_pairs(dk0, dv0, dk1, dv1, true, nullptr, (unsigned)g->n, 32, hist,
+                         kRadixItemsSmall, dblocks, &alt, st);
     if (e != cudaSuccess) return e;
     const uint32_t *order = alt ? dv1 : dv0;
     // 2. emit (tile, Gaussian) pairs in depth order
@@ -263,8 +265,9 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
     uint32_t *pk0 = (uint32_t *)(ws + p.off_pkey[0]), *pv0 = (uint32_t *)(ws + p.off_pval[0]);
     uint32_t *pk1 = (uint32_t *)(ws + p.off_pkey[1]), *pv1 = (uint32_t *)(ws + p.off_pval[1]);
     alt = false;
+    const int pblocks = (int)(((int64_t)p.pair_cap + kRadixBlock - 1) / kRadixBlock);
     e = radix_sort_pairs(pk0, pv0, pk1, pv1, false, &ctrl->n_pairs, p.pair_cap, tbits, hist,
-                         p.radix_blocks_max, &alt, st);
+                         kRadixItems, pblocks, &alt, st);
     if (e != cudaSuccess) return e;
     const uint32_t *pk_sorted = alt ? pk1 : pk0;
     pval_sorted = alt ? pv1 : pv0;

@@ -14,8 +14,10 @@ constexpr int kTile = GDGS_TILE;        // raster tile edge (pixels)
 constexpr int kMaxCycles = 64;          // bound on V-cycles per solve
 constexpr int kMaxLevels = 24;          // bound on multigrid levels
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;         // keys per thread per radix block
+constexpr int kRadixItems = 8;          // keys per thread per radix block (pair sort)
 constexpr int kRadixBlock = kRadixThreads * kRadixItems;
+constexpr int kRadixItemsSmall = 2;     // depth sort (fewer keys): more, shorter blocks
+constexpr int kRadixBlockSmall = kRadixThreads * kRadixItemsSmall;
 constexpr int kBinBlock = 256;  // Gaussians per block of the pair count and emission
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
@@ -174,12 +176,14 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t st);
 
 // Stable LSD radix sort of 32-bit keys with 32-bit values over bits
 // [0, nbits). n = min(*n_dev, cap) if n_dev else cap. vals_in == nullptr means
-// the values are the element indices. Returns in *out_is_alt whether the
+// the values are the element indices. Blocks of kRadixThreads * items keys
+// (items kRadixItems or kRadixItemsSmall), max_blocks of them at most; hist
+// holds 256 * (max_blocks + 1) words. Returns in *out_is_alt whether the
 // result sits in the alternate buffers.
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                              uint32_t *vals_alt, bool implicit_vals,
                              const unsigned long long *n_dev, unsigned cap, int nbits,
-                             uint32_t *hist, int max_blocks, bool *out_is_alt,
+                             uint32_t *hist, int items, int max_blocks, bool *out_is_alt,
                              cudaStream_t st);
 
 struct BinArgs {

@@ -15,6 +15,8 @@
 // stable: items are taken in rounds of 256 consecutive keys; within a warp peers
 // of a digit are found with __match_any_sync and ranked by lane; warps are
 // ranked in order through a shared-memory prefix per digit.
+#include <algorithm>
+
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -33,19 +35,20 @@ __device__ __forceinline__ unsigned item_count(const unsigned long long *n_dev, 
   return n < cap ? (unsigned)n : cap;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads)
 radix_hist_kernel(const uint32_t *keys, const unsigned long long *n_dev, unsigned cap,
                   int shift, unsigned mask, uint32_t *hist) {
   griddep_enter();
   __shared__ unsigned sh[256];
   const unsigned n = item_count(n_dev, cap);
-  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  const unsigned nb = (n + kRadixThreads * ITEMS - 1) / (kRadixThreads * ITEMS);
   if (blockIdx.x >= nb) return;
   sh[threadIdx.x] = 0;
   __syncthreads();
-  const unsigned base = blockIdx.x * kRadixBlock;
+  const unsigned base = blockIdx.x * (kRadixThreads * ITEMS);
 #pragma unroll 4
-  for (int r = 0; r < kRadixItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const unsigned i = base + r * kRadixThreads + threadIdx.x;
     if (i < n) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
   }
@@ -78,11 +81,12 @@ __device__ __forceinline__ unsigned scan256(unsigned v, unsigned *total) {
 
 // Per digit d (one CTA each): exclusive scan of the block counts hist[d nb ..]
 // in place; the digit's total goes to tot[d].
+template <int ITEMS>
 __global__ void __launch_bounds__(256)
 radix_scan_digit_kernel(uint32_t *hist, uint32_t *tot, const unsigned long long *n_dev, unsigned cap) {
   griddep_enter();
   const unsigned n = item_count(n_dev, cap);
-  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  const unsigned nb = (n + kRadixThreads * ITEMS - 1) / (kRadixThreads * ITEMS);
   uint32_t *h = hist + (size_t)blockIdx.x * nb;
   unsigned run = 0;
   for (unsigned base = 0; base < nb; base += 256) {
@@ -105,6 +109,7 @@ __global__ void __launch_bounds__(256) radix_scan_top_kernel(uint32_t *tot, unsi
   if (threadIdx.x < ndig) tot[threadIdx.x] = ex;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                      uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
@@ -114,12 +119,12 @@ radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t 
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kWarps][256];
   const unsigned n = item_count(n_dev, cap);
-  const unsigned nb = (n + kRadixBlock - 1) / kRadixBlock;
+  const unsigned nb = (n + kRadixThreads * ITEMS - 1) / (kRadixThreads * ITEMS);
   if (blockIdx.x >= nb) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x <= mask) run[threadIdx.x] = dbase[threadIdx.x] + hist[threadIdx.x * nb + blockIdx.x];
-  const unsigned base = blockIdx.x * kRadixBlock;
-  for (int r = 0; r < kRadixItems; ++r) {
+  const unsigned base = blockIdx.x * (kRadixThreads * ITEMS);
+  for (int r = 0; r < ITEMS; ++r) {
     const unsigned i = base + r * kRadixThreads + threadIdx.x;
     if (base + r * kRadixThreads >= n) break;  // uniform across the block
     const bool valid = i < n;
@@ -182,7 +187,7 @@ __device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigne
   return x - v + before;
 }
 
-// Sum of tile counts per block of kRadixBlock depth-ordered Gaussians.
+// Sum of tile counts per block of kBinBlock depth-ordered Gaussians.
 // The tiles a splat reaches: per row of tiles of its footprint box, the run of
 // tiles whose box of pixel centres meets the ellipse p <= cut', where p = A dx^2
 // + B dx dy + C dy^2 is the splat's exponent (conic with k log2 e folded in) and
@@ -341,47 +346,46 @@ __global__ void __launch_bounds__(kBinBlock) emit_kernel(BinArgs a) {
   }
 }
 
-// Tile ranges by binary search in the tile-sorted keys; compaction of the
-// non-empty tiles into `active` (order irrelevant: tiles are independent).
+// Tile ranges from the boundaries in the tile-sorted keys, one pass over the
+// pairs: pair i starts its tile's run when key[i-1] differs and ends it when
+// key[i+1] differs. Ranges and mask are zeroed beforehand, so tiles without
+// pairs read (0, 0) and 0. A run's first pair also appends its tile to
+// `active` (order irrelevant: tiles are independent).
 __global__ void __launch_bounds__(256)
-ranges_kernel(const uint32_t *keys, Ctrl *ctrl, unsigned cap, int T, uint2 *range,
-              uint32_t *active, uint8_t *mask) {
+ranges_kernel(const uint32_t *keys, Ctrl *ctrl, unsigned cap, uint2 *range, uint32_t *active,
+              uint8_t *mask) {
   griddep_enter();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned long long np = ctrl->n_pairs;
   const unsigned n = np < cap ? (unsigned)np : cap;
-  bool act = false;
-  if (t < T) {
-    unsigned lo = 0, hi = n;
-    while (lo < hi) {  // first index with key >= t
-      const unsigned mid = (lo + hi) >> 1;
-      if (keys[mid] < (unsigned)t) lo = mid + 1; else hi = mid;
-    }
-    const unsigned s = lo;
-    hi = n;
-    while (lo < hi) {  // first index with key > t
-      const unsigned mid = (lo + hi) >> 1;
-      if (keys[mid] <= (unsigned)t) lo = mid + 1; else hi = mid;
-    }
-    range[t] = make_uint2(s, lo);
-    act = lo > s;
-    mask[t] = act ? 1 : 0;
-  }
-  const unsigned ball = __ballot_sync(0xffffffffu, act);
-  unsigned base = 0;
+  unsigned *rw = reinterpret_cast<unsigned *>(range);
   const int lane = threadIdx.x & 31;
-  if (lane == 0 && ball) base = atomicAdd(&ctrl->n_active, __popc(ball));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (act) active[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)t;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // uniform per warp
+    const unsigned i = i0 + threadIdx.x;
+    const bool in = i < n;
+    const uint32_t k = in ? keys[i] : 0u;
+    const bool start = in && (i == 0 || keys[i - 1] != k);
+    const bool end = in && (i + 1 == n || keys[i + 1] != k);
+    if (start) {
+      rw[2 * (size_t)k] = i;
+      mask[k] = 1;
+    }
+    if (end) rw[2 * (size_t)k + 1] = i + 1;
+    const unsigned ball = __ballot_sync(0xffffffffu, start);
+    unsigned base = 0;
+    if (lane == 0 && ball) base = atomicAdd(&ctrl->n_active, __popc(ball));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (start) active[base + __popc(ball & ((1u << lane) - 1u))] = k;
+  }
 }
 
 }  // namespace
 
-cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
-                             uint32_t *vals_alt, bool implicit_vals,
-                             const unsigned long long *n_dev, unsigned cap, int nbits,
-                             uint32_t *hist, int max_blocks, bool *out_is_alt,
-                             cudaStream_t st) {
+template <int ITEMS>
+cudaError_t radix_sort_t(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                         bool implicit_vals, const unsigned long long *n_dev, unsigned cap,
+                         int nbits, uint32_t *hist, int max_blocks, bool *out_is_alt,
+                         cudaStream_t st) {
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   bool alt = false;
   bool first = true;
@@ -390,13 +394,13 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     const int bits = nbits - shift < 8 ? nbits - shift : 8;
     const unsigned mask = (1u << bits) - 1u;
     if (blocks == 0) break;
-    { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
+    { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
     uint32_t *dtot = hist + (size_t)256 * max_blocks;
-    { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
+    { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel<ITEMS>, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
     { LaunchScope ls_("radix_scan_top", st); launch_k(radix_scan_top_kernel, 1, 256, 0, st, dtot, mask + 1); }
     {
       LaunchScope ls_("radix_scatter", st);
-      launch_k(radix_scatter_kernel, blocks, kRadixThreads, 0, st,
+      launch_k(radix_scatter_kernel<ITEMS>, blocks, kRadixThreads, 0, st,
           ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist, dtot);
     }
     first = false;
@@ -406,6 +410,20 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
   }
   *out_is_alt = alt;
   return cudaGetLastError();
+}
+
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                             uint32_t *vals_alt, bool implicit_vals,
+                             const unsigned long long *n_dev, unsigned cap, int nbits,
+                             uint32_t *hist, int items, int max_blocks, bool *out_is_alt,
+                             cudaStream_t st) {
+  if (items == kRadixItemsSmall)
+    return radix_sort_t<kRadixItemsSmall>(keys, vals, keys_alt, vals_alt, implicit_vals, n_dev,
+                                          cap, nbits, hist, max_blocks, out_is_alt, st);
+  if (items == kRadixItems)
+    return radix_sort_t<kRadixItems>(keys, vals, keys_alt, vals_alt, implicit_vals, n_dev, cap,
+                                     nbits, hist, max_blocks, out_is_alt, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st) {
@@ -420,7 +438,12 @@ cudaError_t launch_emit_pairs(const BinArgs &a, cudaStream_t st) {
 cudaError_t launch_tile_ranges(const uint32_t *sorted_keys, Ctrl *ctrl, unsigned pair_cap,
                                int T, uint2 *range, uint32_t *active, uint8_t *mask,
                                cudaStream_t st) {
-  { LaunchScope ls_("tile_ranges", st); launch_k(ranges_kernel, (T + 255) / 256, 256, 0, st, sorted_keys, ctrl, pair_cap, T, range, active, mask); }
+  cudaError_t e = cudaMemsetAsync(range, 0, 8 * (size_t)T, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mask, 0, (size_t)T, st);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)std::min<unsigned long long>((pair_cap + 255ull) / 256, 2048);
+  if (blocks == 0) return cudaSuccess;
+  { LaunchScope ls_("tile_ranges", st); launch_k(ranges_kernel, blocks, 256, 0, st, sorted_keys, ctrl, pair_cap, range, active, mask); }
   return cudaGetLastError();
 }
 
