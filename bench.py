@@ -438,28 +438,60 @@ def main():
     value = agg["value"]
     st = r.stats()
 
-    # end to end through the public API with host buffers: pinned H2D of the scene,
-    # the render, D2H of the image, all inside the timed region
-    host = {k: torch.as_tensor(getattr(scene, k)).pin_memory() for k in
-            ("mean", "scale", "quat", "opacity", "grad")}
-    host_img = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
-    dev_in = G.DeviceGaussians(*(torch.empty_like(host[k], device=dev) for k in
-                                 ("mean", "scale", "quat", "opacity", "grad")))
+    # end to end through the public API with host buffers: every step copies the scene
+    # from pinned host memory, renders, and copies the image back, all inside the timed
+    # region. Steps are pipelined over two buffer sets: the copy-in of step s + 1 (its own
+    # stream) and the copy-out of step s - 1 (another stream) overlap the render of step s;
+    # renders themselves run one after another on the render stream.
+    keys = ("mean", "scale", "quat", "opacity", "grad")
+    host = {k: torch.as_tensor(getattr(scene, k)).pin_memory() for k in keys}
+    host_img = [torch.empty((C, H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+    dev_in = [G.DeviceGaussians(*(torch.empty_like(host[k], device=dev) for k in keys))
+              for _ in range(2)]
+    outs = [torch.empty_like(out) for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = host_img.numel() * 4
+    d2h = host_img[0].numel() * 4
+    for i in range(2):  # capture both buffer sets' graphs outside the timed region
+        for k in keys:
+            getattr(dev_in[i], k).copy_(host[k])
+        r.render_view(dev_in[i], cam, mean, outs[i])
     torch.cuda.synchronize()
+    h2d_st = torch.cuda.Stream(device=dev)
+    d2h_st = torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(e2e_steps):
-        for k in ("mean", "scale", "quat", "opacity", "grad"):
-            getattr(dev_in, k).copy_(host[k], non_blocking=True)
-        r.render_view(dev_in, cam, mean, out)
-        host_img.copy_(out, non_blocking=True)
+    h2d_st.wait_stream(stream)
+    d2h_st.wait_stream(stream)
+    for s_ in range(e2e_steps):
+        i = s_ & 1
+        with torch.cuda.stream(h2d_st):
+            if s_ >= 2:
+                h2d_st.wait_event(ev_done[i])  # the render that read this buffer set is done
+            for k in keys:
+                getattr(dev_in[i], k).copy_(host[k], non_blocking=True)
+            ev_in[i].record(h2d_st)
+        stream.wait_event(ev_in[i])
+        if s_ >= 2:
+            stream.wait_event(ev_out[i])  # the image in this buffer set has been copied out
+        r.render_view(dev_in[i], cam, mean, outs[i])
+        ev_done[i].record(stream)
+        with torch.cuda.stream(d2h_st):
+            d2h_st.wait_event(ev_done[i])
+            host_img[i].copy_(outs[i], non_blocking=True)
+            ev_out[i].record(d2h_st)
+    stream.wait_stream(d2h_st)
+    stream.wait_stream(h2d_st)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b)
+    last = (e2e_steps - 1) & 1  # the copied-out image is the rendered one
+    if not torch.equal(host_img[last], outs[last].cpu()):
+        raise RuntimeError("end-to-end: the image copied to the host differs from the render")
     e2e_value = replicas.aggregate(float(e2e_steps), e2e_ms / 1e3, device=dev)["value"]
 
     # per-kernel CUDA-event times (outside the timed region). Profiling launches
