@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
         if (p2 > ge2.z) continue;
         const float al = fminf(amax, ge2.y * ex2_approx_b(-p2));
         if (al < amin) continue;
-        T = T * (1.f - al);
+        T = __fsub_rn(T, __fmul_rn(al, T));  // exactly as the forward rasteriser
         last = (int)(s + k);
         if (T < tmin) {
           done = true;

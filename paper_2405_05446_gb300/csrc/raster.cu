@@ -6,7 +6,7 @@
 // batches of 256 into shared memory and every pixel composites them as in
 // Eq. gdgs2d (Eq. color with the gradient attribute):
 //   G = exp(-k d^T conic d), a = min(alpha_max, alpha G), skip a < alpha_min,
-//   acc += g a T, T *= (1 - a), stop once T < t_min.
+//   acc += g a T, T -= a T, stop once T < t_min.
 // Tiles no splat reaches are never launched (the field is sparse, Sec. 2.2).
 //
 // The splat centre is staged relative to the tile origin from its (hi, lo) pair,
@@ -82,16 +82,16 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
         if (p2 > ge2.z) continue;
         const float al = fminf(amax, ge2.y * ex2_approx(-p2));
         if (al < amin) continue;
-        const float w = al * T;
+        const float w = __fmul_rn(al, T);
 #pragma unroll
         for (int v = 0; v < QV; ++v) {
           const float4 gg = s_g[v][k];
-          acc[4 * v] = fmaf(gg.x, w, acc[4 * v]);
-          acc[4 * v + 1] = fmaf(gg.y, w, acc[4 * v + 1]);
-          acc[4 * v + 2] = fmaf(gg.z, w, acc[4 * v + 2]);
-          acc[4 * v + 3] = fmaf(gg.w, w, acc[4 * v + 3]);
+          const float gq[4] = {gg.x, gg.y, gg.z, gg.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (4 * v + c < Q) acc[4 * v + c] = fmaf(gq[c], w, acc[4 * v + c]);
         }
-        T = T * (1.f - al);
+        T = __fsub_rn(T, w);  // T (1 - a), reusing the weight (the backward replays this)
         if (T < tmin) {
           done = true;
           break;
