@@ -919,7 +919,7 @@ struct UpShape {
 // operator, transfers and sweep order are those of the tiled kernels (same
 // coef, residual and prolong1d), on the natural row-major layout.
 
-constexpr long long kTailCells = 12288;
+constexpr long long kTailCells = 4096;
 constexpr int kTailThreads = 1024;
 
 struct TailArgs {
