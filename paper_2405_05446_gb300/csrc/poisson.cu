@@ -508,6 +508,49 @@ __device__ __forceinline__ void half_sweep(float *U, const float *F, const Facto
   }
 }
 
+// The first half-sweep of a down pass (colour col) on u = 0: the same values
+// half_sweep computes from zero neighbours, omega (-f / d) with the same
+// rounding (-f / 4 away from the border), from f alone; the other colour and the
+// halo stay 0.
+template <class G>
+__device__ __forceinline__ void half_sweep_from_zero(float *U, const float *F,
+                                                     const Factors<G> *fa, const LevelGeom &g,
+                                                     int ry0, int rx0, int col, float omega) {
+  constexpr int NU_ = (G::RY - 2) * G::NQ;
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int idx = tid; idx < NU_; idx += kMgThreads) {
+    const int y = 1 + idx / G::NQ;
+    const int q = idx - (y - 1) * G::NQ;
+    const int m0 = q * 4;
+    const int gy = ry0 + y;
+    const bool updE = ((gy + rx0) & 1) == col;
+    const int tp = updE ? 0 : G::PLANE;
+    const float4 f = *reinterpret_cast<const float4 *>(F + tp + y * G::S + 4 + m0);
+    const int gx0 = rx0 + 2 * m0;
+    float4 r;
+    if (gy >= 1 && gy <= g.H - 3 && gx0 >= 1 && gx0 + 7 <= g.W - 3) {
+      r = make_float4(0.25f * (0.f - f.x), 0.25f * (0.f - f.y), 0.25f * (0.f - f.z),
+                      0.25f * (0.f - f.w));
+      if (omega != 1.f)
+        r = make_float4(__fmul_rn(omega, r.x), __fmul_rn(omega, r.y), __fmul_rn(omega, r.z),
+                        __fmul_rn(omega, r.w));
+    } else {
+      const int pl = updE ? 0 : 1;
+      const float wy = fa->wy[y], cS = fa->cS[y], cN = fa->cN[y];
+      const float4 wx = fa->wx[pl][q], cE = fa->cE[pl][q], cW = fa->cW[pl][q];
+#define GDGS_CELL0(C)                                                              \
+  {                                                                               \
+    const float ae = wy * cE.C, aw = wy * cW.C, as = wx.C * cS, an = wx.C * cN;   \
+    const float d = (ae + aw) + (as + an);                                        \
+    r.C = d > 0.f ? __fmul_rn(omega, (0.f - f.C) / d) : 0.f;                      \
+  }
+      GDGS_CELL0(x) GDGS_CELL0(y) GDGS_CELL0(z) GDGS_CELL0(w)
+#undef GDGS_CELL0
+    }
+    *reinterpret_cast<float4 *>(U + tp + y * G::S + 4 + m0) = r;
+  }
+}
+
 // Residual f - L u at region cell (y, x) (grid cell (gy, gx) in the grid).
 template <class G>
 __device__ __forceinline__ float tile_residual(float *U, float *F, const LevelGeom &g, int y, int x,
@@ -813,8 +856,10 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
   zero_split<G>(U);
   build_factors<G>(fa, g, ry0, rx0);
   __syncthreads();
+  half_sweep_from_zero<G>(U, F, fa, g, ry0, rx0, 0, a.omega);
+  __syncthreads();
 #pragma unroll
-  for (int s = 0; s < 2 * NU; ++s) {
+  for (int s = 1; s < 2 * NU; ++s) {
     half_sweep<G>(U, F, fa, g, ry0, rx0, s & 1, a.omega);
     __syncthreads();
   }
