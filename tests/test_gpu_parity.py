@@ -153,6 +153,33 @@ def test_poisson_matches_dct_oracle(hw):
     np.testing.assert_allclose(img.mean(axis=(1, 2)), mean, atol=1e-6)
 
 
+def test_pixel_kernels_alignment_contract():
+    """Maps and image must be 16-byte aligned (then rows of a multiple of 4 floats take
+    the four-pixel divergence and finalisation; other widths the one-pixel kernels, both
+    covered against the oracle by the shapes above). A pointer one float past a 16-byte
+    boundary is rejected on the host with GDGS_ERR_INVALID_ARG, before anything runs."""
+    H, W = 270, 480
+    rng = np.random.default_rng(7)
+    maps = torch.from_numpy(rng.laplace(0, 0.1, (3, 2, H, W)).astype(np.float32)).cuda()
+    mean = [0.5, 0.1, -0.2]
+    sopts = G.solver_opts()
+    ws = torch.empty(G.workspace_size(0, 3, W, H, None, sopts), dtype=torch.uint8, device="cuda")
+    img = torch.empty((3, H, W), device="cuda")
+    G.poisson_reconstruct(maps, mean, img, ws, sopts=sopts)
+    st = G.sync_status(ws)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
+    ref = O.poisson_neumann(O.divergence(maps.cpu().numpy().astype(np.float64)), mean)
+    assert img_err(img.cpu().numpy().astype(np.float64), ref)[0] <= IMG_TOL
+    mbuf = torch.empty(maps.numel() + 1, device="cuda")
+    maps_s = mbuf[1:].view(maps.shape)
+    ibuf = torch.empty(img.numel() + 1, device="cuda")
+    img_s = ibuf[1:].view(img.shape)
+    for m, o in ((maps_s, img), (maps, img_s)):
+        with pytest.raises(G.GDGSError) as ei:
+            G.poisson_reconstruct(m, mean, o, ws, sopts=sopts)
+        assert ei.value.code == 1  # GDGS_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("hw", [(2, 12000), (12000, 2)])
 def test_poisson_long_strip(hw):
     """Strips whose small levels do not fit the one-CTA tail with their coefficient
