@@ -107,6 +107,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
     }
     p->off_hist = cv.take(4 * 256 * (size_t)(p->radix_blocks_max + 1));
     p->off_blocksum = cv.take(8 * (size_t)((n + kBinBlock - 1) / kBinBlock + 2));
+    p->off_gtiles = cv.take(4 * (size_t)n);
     p->off_maps = cv.take(4 * (size_t)C * 2 * W * H);
     p->off_dsplat = cv.take(24 * (size_t)n);
   }
@@ -254,6 +255,7 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
     b.T = p.T;
     b.pair_cap = p.pair_cap;
     b.blocksum = (unsigned long long *)(ws + p.off_blocksum);
+    b.tiles = (uint32_t *)(ws + p.off_gtiles);
     b.pkey = (uint32_t *)(ws + p.off_pkey[0]);
     b.pval = (uint32_t *)(ws + p.off_pval[0]);
     b.ctrl = ctrl;

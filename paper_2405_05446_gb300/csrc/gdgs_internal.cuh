@@ -125,6 +125,7 @@ struct Plan {
   size_t off_dkey[2], off_dval[2];                     // depth sort [n]
   size_t off_hist;                                     // radix histograms
   size_t off_blocksum;                                 // scan partials
+  size_t off_gtiles;                                   // tiles per depth-ordered Gaussian
   size_t off_pkey[2], off_pval[2];                     // pairs [pair_cap]
   size_t off_range, off_active, off_mask;              // per tile
   size_t off_maps;                                     // [C][2][H][W]
@@ -197,6 +198,7 @@ struct BinArgs {
   int tiles_x, T;
   unsigned pair_cap;
   unsigned long long *blocksum;  // [ceil(n / kBinBlock) + 1]
+  uint32_t *tiles;         // [n] tiles each depth-ordered Gaussian reaches (count -> emit)
   uint32_t *pkey, *pval;   // emitted pairs
   Ctrl *ctrl;
 };

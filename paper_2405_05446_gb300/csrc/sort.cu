@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(kBinBlock) count_kernel(BinArgs a) {
     const uint32_t g = a.order[i];
     const uint2 rc = a.rect[g];
     if (rect_tiles(rc)) s = tiles_hit(a, g, rc);
+    a.tiles[i] = (uint32_t)s;
   }
   unsigned long long tot;
   block_exclusive_scan(s, &tot);
@@ -324,11 +325,12 @@ __global__ void __launch_bounds__(kBinBlock) emit_kernel(BinArgs a) {
   const bool in = i < a.n;
   uint32_t g = 0;
   uint2 rc = make_uint2(0, 0);
+  unsigned cnt = 0u;
   if (in) {
     g = a.order[i];
     rc = a.rect[g];
+    cnt = a.tiles[i];  // as counted by count_kernel
   }
-  const unsigned cnt = (in && rect_tiles(rc)) ? tiles_hit(a, g, rc) : 0u;
   unsigned long long tot;
   const unsigned long long my = a.blocksum[blockIdx.x] + block_exclusive_scan(cnt, &tot);
   if (cnt) {
