@@ -153,18 +153,6 @@ __device__ __forceinline__ bool interior(const LevelGeom &g, int I, int J) {
   return I > 0 && J > 0 && I < g.H - 2 && J < g.W - 2;
 }
 
-__device__ __forceinline__ bool in_grid(const LevelGeom &g, int I, int J) {
-  return I >= 0 && J >= 0 && I < g.H && J < g.W;
-}
-
-__device__ __forceinline__ float gs_value(const LevelGeom &g, int I, int J, float uE, float uW,
-                                          float uS, float uN, float f) {
-  if (interior(g, I, J)) return 0.25f * ((uE + uW) + (uS + uN) - f);
-  const Coef c = coef(g, I, J);
-  const float d = c.e + c.w + c.s + c.n;
-  return d > 0.f ? (c.e * uE + c.w * uW + c.s * uS + c.n * uN - f) / d : 0.f;
-}
-
 // Differences to the centre keep the rounding relative to L u, not to u: a
 // correction as large as the image itself still gets an accurate residual.
 __device__ __forceinline__ float residual(const LevelGeom &g, int I, int J, float u, float uE,

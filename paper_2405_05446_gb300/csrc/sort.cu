@@ -121,7 +121,7 @@ radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t 
   const unsigned n = item_count(n_dev, cap);
   const unsigned nb = (n + kRadixThreads * ITEMS - 1) / (kRadixThreads * ITEMS);
   if (blockIdx.x >= nb) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   if (threadIdx.x <= mask) run[threadIdx.x] = dbase[threadIdx.x] + hist[threadIdx.x * nb + blockIdx.x];
   const unsigned base = blockIdx.x * (kRadixThreads * ITEMS);
   for (int r = 0; r < ITEMS; ++r) {
