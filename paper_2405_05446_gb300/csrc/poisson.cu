@@ -219,6 +219,30 @@ __device__ __forceinline__ bool block_should_stop(Ctrl *ctrl, int k, int first) 
   return s_stop != 0;
 }
 
+// Two block-wide sums in one pass; valid in the first thread of the block.
+__device__ void block_sum2(float &a, float &b) {
+  __shared__ float2 part2[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  const int lane = tid & 31, w = tid >> 5;
+  __syncthreads();
+  if (lane == 0) part2[w] = make_float2(a, b);
+  __syncthreads();
+  float sa = 0.f, sb = 0.f;
+  if (tid == 0)
+    for (int i = 0; i < (nthreads + 31) / 32; ++i) {
+      sa += part2[i].x;
+      sb += part2[i].y;
+    }
+  a = sa;
+  b = sb;
+}
+
 // Block-wide sum; the result is valid in the first thread of the block.
 __device__ float block_sum(float v) {
   __shared__ float part[32];
@@ -770,10 +794,11 @@ __device__ __forceinline__ void finest_epilogue4(const float *U, const float *F,
     *reinterpret_cast<float4 *>(ul + p) = make_float4(lv[0], lv[1], lv[2], lv[3]);
     *reinterpret_cast<float4 *>(rn + p) = make_float4(r[0], r[1], r[2], r[3]);
   }
-  su = block_sum(su);
-  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
-  rn2 = block_sum(rn2);
-  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+  block_sum2(su, rn2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+    atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+  }
 }
 
 // ------------------------------------------------------------------ level kernels
@@ -858,7 +883,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_down_kernel(LvArgs a, Ctrl *ctr
 // Up: u += P u_{l+1}, nu2 sweeps, write u. On the finest level instead:
 // u_{k+1} = u_k + e (float-float), r_{k+1} = r_k - L e, ||r_{k+1}||^2, sum(u_{k+1}).
 template <int NU, int TY_, int TX_>
-__global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
+__global__ void __launch_bounds__(kMgThreads, 4) mg_up_kernel(LvArgs a, Ctrl *ctrl, int k_in) {
   griddep_enter();
   using G = Geo<NU, TY_, TX_>;
   extern __shared__ float4 sm4[];
@@ -926,10 +951,11 @@ __global__ void __launch_bounds__(kMgThreads) mg_up_kernel(LvArgs a, Ctrl *ctrl,
       rn[p] = r;
       rn2 = fmaf(r, r, rn2);
     }
-  su = block_sum(su);
-  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
-  rn2 = block_sum(rn2);
-  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+  block_sum2(su, rn2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    atomicAdd(&ctrl->sum_u[k + 1][c], (double)su);
+    atomicAdd(&ctrl->rnorm2[k + 1], (double)rn2);
+  }
 }
 
 template <class G>
