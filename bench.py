@@ -97,7 +97,7 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-TAIL_CELLS = 12288  # levels with at most this many cells per channel run in the tail kernel
+TAIL_CELLS = 4096  # levels with at most this many cells per channel run in the tail kernel
 
 
 def mg_levels(H: int, W: int, coarse_max: int = 8):
