@@ -247,7 +247,8 @@ GDGS_API int gdgs_render_view(const gdgs_gaussians *g, const gdgs_camera *cam, c
  * near_plane; its width and height must equal cam's. Because no camera value is
  * baked into the launches, a CUDA graph captured from one call (the multigrid
  * cycle loop is then recorded as a conditional WHILE node) replays correctly for
- * any camera written to cam_dev before the replay. Errors as gdgs_render_view. */
+ * any camera written to cam_dev before the replay. cam_dev's values cannot be checked
+ * on the host: a near_plane below 0 (or NaN) is read as 0. Errors as gdgs_render_view. */
 GDGS_API int gdgs_render_view_devcam(const gdgs_gaussians *g, const gdgs_camera *cam,
                                      const gdgs_camera *cam_dev, const float *mean,
                                      const gdgs_raster_opts *ropts,

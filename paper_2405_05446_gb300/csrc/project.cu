@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
     a.fy = __ldg(&cd->fy);
     a.cx = __ldg(&cd->cx);
     a.cy = __ldg(&cd->cy);
-    a.znear = __ldg(&cd->near_plane);
+    // not validated on the host: a negative or NaN near plane reads as 0, so the
+    // depth keys of visible Gaussians stay positive floats (their bits sort)
+    a.znear = fmaxf(__ldg(&cd->near_plane), 0.f);
   }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool visible = false;

@@ -85,6 +85,32 @@ def test_captured_view_graph_replays_any_camera(_lib):
 
 
 @pytest.mark.gpu
+def test_device_camera_near_plane_below_zero_reads_as_zero(_lib):
+    """The device camera cannot be validated on the host: a negative (or NaN) near
+    plane is read as 0, which gives exactly the view of a camera with near = 0."""
+    import dataclasses
+    import paper_2405_05446_gb300 as G
+    scene = _scenes()[1]
+    g = G.gaussians_to_device(scene)
+    W, H = 160, 96
+    cam0 = S.look_at_camera((0.4, 0.1, -2.0), (0.0, 0.0, 0.0), W, H, near=0.0)
+    ro, so = G.raster_opts(), G.solver_opts()
+    nb = G.workspace_size(scene.n, 3, W, H, ro, so)
+    out = {}
+    for name, near in (("zero", 0.0), ("negative", -1.0), ("nan", float("nan"))):
+        cam = dataclasses.replace(cam0, near=near)
+        cam_dev = torch.as_tensor(np.frombuffer(G.camera_bytes(cam), dtype=np.uint8).copy()).cuda()
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        img = torch.empty((3, H, W), device="cuda")
+        G.render_view_devcam(g, cam0, cam_dev, [0.5] * 3, img, ws, ro, so)
+        st = G.sync_status(ws)
+        assert st["status"] == 0, (name, st)
+        out[name] = img.cpu()
+    assert torch.equal(out["negative"], out["zero"])
+    assert torch.equal(out["nan"], out["zero"])
+
+
+@pytest.mark.gpu
 def test_served_views_identical_alone_and_in_the_mix(_lib):
     from paper_2405_05446_gb300 import serving as SV
     scenes = _scenes()
