@@ -40,8 +40,9 @@ _LIB = os.path.join(_HERE, "_oracle_raster.so")
 _lib = None
 
 # column indices of a projected-Gaussian row (mirrors the enum in oracle_raster.c)
-VALID, DEPTH, MX, MY, CA, CB, CC, OPA, XMIN, XMAX, YMIN, YMAX, S00, S01, S11, KEY = range(16)
-STRIDE = 16
+(VALID, DEPTH, MX, MY, CA, CB, CC, OPA, XMIN, XMAX, YMIN, YMAX, S00, S01, S11, DERR, KAPPA,
+ GHOST, NEARAMB, BOXW, TZ0, TZ1, TZ2, LMAX) = range(24)
+STRIDE = 24
 
 
 @dataclasses.dataclass
@@ -93,12 +94,20 @@ def camera_array(cam) -> np.ndarray:
     return np.concatenate([w, [cam.fx, cam.fy, cam.cx, cam.cy, cam.near]]).astype(np.float64)
 
 
-def project(scene, cam, opts: RasterOpts = RasterOpts()) -> np.ndarray:
+# relative precision of a plain float32 evaluation of the depth w20 x + w21 y + w22 z + w23
+DEPTH_REL_F32 = 4.0 * 2.0 ** -24 / (1.0 - 4.0 * 2.0 ** -24)
+
+
+def project(scene, cam, opts: RasterOpts = RasterOpts(),
+            depth_rel: float = DEPTH_REL_F32) -> np.ndarray:
     """Per-Gaussian projection rows [N][STRIDE] (Eq. 3dgs, Eq. sig2d).
 
     Culls: non-normalisable quaternion, camera-space depth <= near, det(Sigma2D) <= 0,
     opacity < alpha_min. Footprint box: the exact bounding box of the ellipse where
     opacity * exp(-exp_coef * d^T Sigma2D^-1 d) >= alpha_min.
+    depth_rel: relative precision of the depth in the implementation under test (for
+    the ambiguity flags only: depth errors up to depth_rel times the sum of the depth's
+    term magnitudes can swap two Gaussians or flip the near cull).
     """
     lib = _load()
     mean, scale, quat, opa = (_f32(scene.mean), _f32(scene.scale), _f32(scene.quat),
@@ -106,26 +115,30 @@ def project(scene, cam, opts: RasterOpts = RasterOpts()) -> np.ndarray:
     n = mean.shape[0]
     out = np.zeros((n, STRIDE), dtype=np.float64)
     camv = camera_array(cam)
-    optv = np.array([opts.dilation, opts.exp_coef, opts.alpha_min], dtype=np.float64)
+    optv = np.array([opts.dilation, opts.exp_coef, opts.alpha_min, depth_rel], dtype=np.float64)
     lib.oracle_project(n, _ptr(mean), _ptr(scale), _ptr(quat), _ptr(opa), _ptr(camv),
                        _ptr(optv), _ptr(out))
     return out
 
 
-def depth_order(proj: np.ndarray) -> np.ndarray:
-    """Valid Gaussians sorted front to back ("sorted from the view direction", Eq. color).
+def depth_order(proj: np.ndarray, ghosts: bool = False) -> np.ndarray:
+    """Valid Gaussians sorted front to back ("sorted from the view direction", Eq. color):
+    ascending FP64 camera depth, equal depths by ascending index.
 
-    The order is an integer decision, so it is taken on the float32 depth key (see
-    oracle_raster.c), the precision the GPU sorts in; equal keys keep ascending index.
+    ghosts=True also lists the Gaussians the near cull removed only within the float32
+    error bound of the depth (see oracle_raster.c); the composite uses them for the
+    ambiguity flag and nothing else.
     """
-    valid = np.nonzero(proj[:, VALID] > 0)[0]
-    key = proj[valid, KEY]
-    return valid[np.lexsort((valid, key))].astype(np.int64)
+    keep = proj[:, VALID] > 0
+    if ghosts:
+        keep |= proj[:, GHOST] > 0
+    idx = np.nonzero(keep)[0]
+    return idx[np.lexsort((idx, proj[idx, DEPTH]))].astype(np.int64)
 
 
 def render_gradients(scene, cam, opts: RasterOpts = RasterOpts(), mode: str = "box",
-                     pixels=None, nthreads: int = 0, amb_rel: float = 2e-5,
-                     depth_rel: float = 0.0, proj=None):
+                     pixels=None, nthreads: int = 0, err_scale: float = 1.0, proj=None,
+                     depth_rel: float = DEPTH_REL_F32):
     """Composite the per-Gaussian attributes front to back (Eq. gdgs2d, Eq. color).
 
     At pixel centre p: for each Gaussian k in depth order, G = exp(-exp_coef d^T conic d)
@@ -136,19 +149,22 @@ def render_gradients(scene, cam, opts: RasterOpts = RasterOpts(), mode: str = "b
     values (Eq. gdgs). mode "all_pairs" visits every Gaussian at every pixel (the plain
     definition); mode "box" skips Gaussians whose footprint box misses the pixel (same
     result). Returns (maps, ambiguous): maps [C][2][H][W] or [C][H][W] (or [P][C][2] /
-    [P][C] for a pixel list), ambiguous a uint8 flag per pixel (see oracle_raster.c).
+    [P][C] for a pixel list), ambiguous a uint8 flag per pixel: one of the discontinuous
+    decisions (near cull, depth order of two contributing Gaussians, alpha vs alpha_min,
+    T vs T_min) lies within its float32 error bound of the threshold (oracle_raster.c
+    derives the bounds; err_scale multiplies them, 0 turns the flags off).
     """
     lib = _load()
     if proj is None:
-        proj = project(scene, cam, opts)
+        proj = project(scene, cam, opts, depth_rel)
     grad = _f32(scene.grad)
     C = grad.shape[1]
     K = grad.shape[2] if grad.ndim == 3 else 1
     Q = C * K
-    order = depth_order(proj)
+    order = depth_order(proj, ghosts=True)
     W, H = cam.width, cam.height
-    optv = np.array([opts.exp_coef, opts.alpha_min, opts.alpha_max, opts.t_min, amb_rel,
-                     depth_rel], dtype=np.float64)
+    optv = np.array([opts.exp_coef, opts.alpha_min, opts.alpha_max, opts.t_min, err_scale],
+                    dtype=np.float64)
     use_box = 1 if mode == "box" else 0
     if mode not in ("box", "all_pairs"):
         raise ValueError(mode)
@@ -253,13 +269,14 @@ def poisson_neumann(rho: np.ndarray, mean) -> np.ndarray:
 
 
 def render_view(scene, cam, mean, opts: RasterOpts = RasterOpts(), nthreads: int = 0,
-                rho_threshold: float = 0.0):
+                rho_threshold: float = 0.0, depth_rel: float = DEPTH_REL_F32):
     """Algorithm 1's render steps: project + composite (Eq. gdgs2d), the Laplacian field
     (the divergence of gradient maps, or the composite itself for Laplacian Gaussians,
     Eq. gdgs), the hard threshold T when rho_threshold > 0 (Eq. thresh), and the Neumann
     Poisson solve (Eq. p2d) with the constant fixed by `mean`.
     Returns (image [C][H][W], maps, ambiguous [H][W])."""
-    maps, amb = render_gradients(scene, cam, opts, mode="box", nthreads=nthreads)
+    maps, amb = render_gradients(scene, cam, opts, mode="box", nthreads=nthreads,
+                                 depth_rel=depth_rel)
     rho = divergence(maps) if maps.ndim == 4 else maps
     if rho_threshold > 0:
         rho = threshold(rho, rho_threshold)

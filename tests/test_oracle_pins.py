@@ -186,7 +186,11 @@ def _hand_rows(alphas, depths, centres, W=8):
     for k, (a, d, (x, y)) in enumerate(zip(alphas, depths, centres)):
         rows[k, O.VALID] = 1
         rows[k, O.DEPTH] = d
-        rows[k, O.KEY] = np.float32(d)
+        rows[k, O.DERR] = 4 * 2.0 ** -24 * abs(d)
+        rows[k, O.KAPPA] = 1.0
+        rows[k, O.LMAX] = 2.0  # Sigma2D = 2 I (conic 0.5 I)
+        rows[k, O.BOXW] = 1.0
+        rows[k, O.TZ0], rows[k, O.TZ1], rows[k, O.TZ2] = x, y, d  # terms of the depth
         rows[k, O.MX], rows[k, O.MY] = x, y
         rows[k, O.CA], rows[k, O.CB], rows[k, O.CC] = 0.5, 0.0, 0.5
         rows[k, O.OPA] = a
@@ -218,6 +222,92 @@ def test_composite_hand_worked_fixture():
     out2, _ = O.render_gradients(_hand_scene(fx["g"][:2]), cam, mode="all_pairs",
                                  pixels=[2 * 8 + 3], proj=rows2)
     assert out2[0, 0, 0] == pytest.approx(fx["expected_two_front"], abs=1e-15)
+
+
+def test_composite_equal_depths_keep_ascending_index():
+    """Equal view depths are composited in ascending Gaussian index (the tie-break
+    reading of "sorted from the view direction", Eq. color), whatever the input."""
+    fx = json.load(open(os.path.join(GOLDEN, "composite_tie.json")))
+    cam = S.tiny_camera(8, 8)
+    c = (3.5, 2.5)
+    # three different centres that all sit on the pixel centre in the hand rows, so
+    # the depth ties are real ties of different Gaussians, not one mean repeated
+    rows = _hand_rows(fx["alpha"], [fx["depth"]] * 3, [c] * 3)
+    rows[:, O.MX] += np.array([0.0, 1e-10, 2e-10])  # distinct; exp(-0.5 dx^2) is 1 in FP64
+    rows[:, O.TZ0] = np.array([0.1, -0.2, 0.3])  # different means whose depths tie
+    out, amb = O.render_gradients(_hand_scene(fx["g"]), cam, mode="all_pairs", pixels=[19],
+                                  proj=rows)
+    assert out[0, 0, 0] == pytest.approx(fx["expected"], abs=1e-15)
+    assert out[0, 0, 0] != pytest.approx(fx["expected_descending"], abs=1e-3)
+    assert amb[0] == 1  # ties between different Gaussians: a float32 sort may order them either way
+    # listing the same three Gaussians in reverse must reverse the composite order
+    rows_r, g_r = rows[::-1].copy(), fx["g"][::-1]
+    out_r, _ = O.render_gradients(_hand_scene(g_r), cam, mode="all_pairs", pixels=[19], proj=rows_r)
+    a, g = fx["alpha"][::-1], g_r
+    want = g[0] * a[0] + g[1] * a[1] * (1 - a[0]) + g[2] * a[2] * (1 - a[0]) * (1 - a[1])
+    assert out_r[0, 0, 0] == pytest.approx(want, abs=1e-15)
+    assert want == pytest.approx(fx["expected_descending"], abs=1e-15)
+    # the same mean twice: equal float32 depths on any evaluation, so no ambiguity
+    rows_same = _hand_rows(fx["alpha"][:2], [fx["depth"]] * 2, [c] * 2)
+    _, amb_same = O.render_gradients(_hand_scene(fx["g"][:2]), cam, mode="all_pairs",
+                                     pixels=[19], proj=rows_same)
+    assert amb_same[0] == 0
+
+
+def test_composite_near_equal_depths_follow_fp64_and_are_flagged():
+    fx = json.load(open(os.path.join(GOLDEN, "composite_tie.json")))
+    cam = S.tiny_camera(8, 8)
+    c = (3.5, 2.5)
+    rows = _hand_rows([0.5, 0.25], [2.0 + 1e-12, 2.0], [c, (3.5 + 1e-10, 2.5)])
+    rows[:, O.TZ0] = [0.1, -0.2]
+    out, amb = O.render_gradients(_hand_scene([1.0, 2.0]), cam, mode="all_pairs", pixels=[19],
+                                  proj=rows)
+    assert out[0, 0, 0] == pytest.approx(fx["near_expected"], abs=1e-15)
+    assert amb[0] == 1
+    # well separated depths: same order, no flag
+    rows = _hand_rows([0.5, 0.25], [2.5, 2.0], [c, (3.5 + 1e-10, 2.5)])
+    out, amb = O.render_gradients(_hand_scene([1.0, 2.0]), cam, mode="all_pairs", pixels=[19],
+                                  proj=rows)
+    assert out[0, 0, 0] == pytest.approx(fx["near_expected"], abs=1e-15)
+    assert amb[0] == 0
+
+
+def test_projected_equal_depths_sort_by_index():
+    """Through the projection: Gaussians at one camera depth (same z, camera looking
+    along +z) get equal FP64 depths and are ordered by index; a farther one goes last."""
+    cam = S.tiny_camera(64, 64)
+    assert _w2c(cam)[2, 0] == 0 and _w2c(cam)[2, 1] == 0
+    n = 4
+    sc = S.Scene(np.float32([[0.05, 0.0, 0.1], [-0.05, 0.02, 0.1], [0.0, -0.03, 0.1],
+                             [0.0, 0.0, 0.0]]),
+                 np.full((n, 3), 0.05, np.float32), np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+                 np.full(n, 0.5, np.float32), np.zeros((n, 1, 2), np.float32))
+    rows = O.project(sc, cam)
+    assert rows[0, O.DEPTH] == rows[1, O.DEPTH] == rows[2, O.DEPTH] > rows[3, O.DEPTH]
+    np.testing.assert_array_equal(O.depth_order(rows), [3, 0, 1, 2])
+    perm = [2, 0, 3, 1]
+    np.testing.assert_array_equal(O.depth_order(rows[perm]), [2, 0, 1, 3])
+
+
+def test_near_cull_within_float32_bound_is_flagged():
+    """A Gaussian whose FP64 depth is within the float32 depth error bound of the near
+    plane is culled (depth <= near) but kept as a ghost that flags the pixels it would
+    reach; one just in front contributes and flags them too."""
+    cam = S.tiny_camera(16, 16)
+    cam.near = 3.0 - 0.0  # the origin sits at depth 3.0 exactly
+    for z, valid in ((0.0, 0), (1e-7, 1)):
+        sc = _one([0, 0, z], [0.05] * 3, [1, 0, 0, 0], opacity=0.8,
+                  grad=np.full((3, 2), 0.5, np.float32))
+        r = O.project(sc, cam)[0]
+        assert r[O.NEARAMB] == 1 and r[O.VALID] == valid and r[O.GHOST] == 1 - valid
+        maps, amb = O.render_gradients(sc, cam)
+        assert amb[8, 8] == 1
+        assert (np.abs(maps).max() > 0) == bool(valid)
+    sc = _one([0, 0, 0.5], [0.05] * 3, [1, 0, 0, 0], opacity=0.8, grad=np.full((3, 2), 0.5, np.float32))
+    r = O.project(sc, cam)[0]
+    assert r[O.NEARAMB] == 0 and r[O.VALID] == 1
+    maps, amb = O.render_gradients(sc, cam)
+    assert amb.max() == 0 and np.abs(maps).max() > 0
 
 
 def test_composite_off_centre_two_splats():
