@@ -350,6 +350,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-views", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--direct-steps", type=int, default=100,
+                    help="views timed through the plain gdgs_render_view call")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="number format of the multigrid corrections and coarse right-hand sides")
     args = ap.parse_args()
@@ -438,6 +440,25 @@ def main():
     value = agg["value"]
     st = r.stats()
 
+    # the same views through the plain C call gdgs_render_view (no whole-view graph:
+    # host-side argument checks, workspace carving and every launch are enqueued per
+    # view; the cycle loop runs as the library's cached WHILE-loop graph)
+    direct_steps = max(1, min(args.steps, args.direct_steps))
+    evd = []
+    for _ in range(direct_steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.render_view(g, cam, mean, out, r.ws, r.ropts, r.sopts)
+        b.record(stream)
+        evd.append((a, b))
+    torch.cuda.synchronize()
+    per_direct = [a.elapsed_time(b) for a, b in evd]
+    value_direct = replicas.aggregate(float(direct_steps), sum(per_direct) / 1e3, device=dev)["value"]
+    if r.stats()["status"] != 0:
+        raise RuntimeError(f"direct render failed: {r.stats()}")
+
     # end to end through the public API with host buffers: every step copies the scene
     # from pinned host memory, renders, and copies the image back, all inside the timed
     # region. Steps are pipelined over two buffer sets: the copy-in of step s + 1 (its own
@@ -458,41 +479,45 @@ def main():
     torch.cuda.synchronize()
     h2d_st = torch.cuda.Stream(device=dev)
     d2h_st = torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    h2d_st.wait_stream(stream)
-    d2h_st.wait_stream(stream)
-    for s_ in range(e2e_steps):
-        i = s_ & 1
-        with torch.cuda.stream(h2d_st):
+
+    def run_e2e(render):
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h2d_st.wait_stream(stream)
+        d2h_st.wait_stream(stream)
+        for s_ in range(e2e_steps):
+            i = s_ & 1
+            with torch.cuda.stream(h2d_st):
+                if s_ >= 2:
+                    h2d_st.wait_event(ev_done[i])  # the render that read this buffer set is done
+                for k in keys:
+                    getattr(dev_in[i], k).copy_(host[k], non_blocking=True)
+                ev_in[i].record(h2d_st)
+            stream.wait_event(ev_in[i])
             if s_ >= 2:
-                h2d_st.wait_event(ev_done[i])  # the render that read this buffer set is done
-            for k in keys:
-                getattr(dev_in[i], k).copy_(host[k], non_blocking=True)
-            ev_in[i].record(h2d_st)
-        stream.wait_event(ev_in[i])
-        if s_ >= 2:
-            stream.wait_event(ev_out[i])  # the image in this buffer set has been copied out
-        r.render_view(dev_in[i], cam, mean, outs[i])
-        ev_done[i].record(stream)
-        with torch.cuda.stream(d2h_st):
-            d2h_st.wait_event(ev_done[i])
-            host_img[i].copy_(outs[i], non_blocking=True)
-            ev_out[i].record(d2h_st)
-    stream.wait_stream(d2h_st)
-    stream.wait_stream(h2d_st)
-    b.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b)
-    last = (e2e_steps - 1) & 1  # the copied-out image is the rendered one
-    if not torch.equal(host_img[last], outs[last].cpu()):
-        raise RuntimeError("end-to-end: the image copied to the host differs from the render")
-    e2e_value = replicas.aggregate(float(e2e_steps), e2e_ms / 1e3, device=dev)["value"]
+                stream.wait_event(ev_out[i])  # the image in this buffer set has been copied out
+            render(dev_in[i], outs[i])
+            ev_done[i].record(stream)
+            with torch.cuda.stream(d2h_st):
+                d2h_st.wait_event(ev_done[i])
+                host_img[i].copy_(outs[i], non_blocking=True)
+                ev_out[i].record(d2h_st)
+        stream.wait_stream(d2h_st)
+        stream.wait_stream(h2d_st)
+        b.record(stream)
+        torch.cuda.synchronize()
+        last = (e2e_steps - 1) & 1  # the copied-out image is the rendered one
+        if not torch.equal(host_img[last], outs[last].cpu()):
+            raise RuntimeError("end-to-end: the image copied to the host differs from the render")
+        return replicas.aggregate(float(e2e_steps), a.elapsed_time(b) / 1e3, device=dev)["value"]
+
+    e2e_value = run_e2e(lambda gi, o: r.render_view(gi, cam, mean, o))
+    e2e_direct = run_e2e(lambda gi, o: G.render_view(gi, cam, mean, o, r.ws, r.ropts, r.sopts))
 
     # per-kernel CUDA-event times (outside the timed region). Profiling launches
     # the cycle loop directly; max_cycles = the observed count keeps it free of
@@ -556,7 +581,16 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                    "render": "Renderer.render_view (one CUDA graph replay per view)"},
+            "value_direct": value_direct,
+            "direct": {"value": value_direct, "unit": "views/s", "steps": direct_steps,
+                       "p50_ms": statistics.median(per_direct),
+                       "p99_ms": float(np.percentile(per_direct, 99)),
+                       "call": "gdgs_render_view per view (CUDA events around the call, L2 flushed)"},
+            "e2e_direct": {"value": e2e_direct, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
+                           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                           "render": "gdgs_render_view per view"},
             "solve": {"cycles": st["cycles"], "rel_residual": st["rel_residual"],
                       "n_pairs": st["n_pairs"], "n_active_tiles": st["n_active_tiles"],
                       "n_visible": st["n_visible"]},
@@ -567,10 +601,11 @@ def main():
         O.build()
         cores = os.cpu_count()
         t0 = time.perf_counter()
-        ref, _, amb = O.render_view(scene, cam, mean, nthreads=cores)
+        ref, _, amb = O.render_view(scene, cam, mean, nthreads=cores, depth_rel=2.0 ** -29)
         tcpu = time.perf_counter() - t0
         img = out.cpu().numpy().astype(np.float64)
         err = float(np.abs(img - ref).max())
+        line["ambiguous_pixel_frac"] = float(amb.mean())
         line["cpu_baseline"] = {"value": 1.0 / tcpu, "unit": "views/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"1 full view of {args.workload} (FP64 box-filtered "

@@ -19,7 +19,10 @@
  *  - Pointers named "device" must point to GPU memory on the current device;
  *    "host" pointers to CPU memory. The library never allocates device memory:
  *    all scratch comes from one caller-owned workspace of gdgs_workspace_size()
- *    bytes (device, 256-byte aligned). Host structs are read during the call only.
+ *    bytes (device, 256-byte aligned). The one exception is the fixed 32 MiB
+ *    array that gdgs_poisson_reconstruct_static uses instead of a workspace,
+ *    reserved on each GPU when the library is loaded. Host structs are read
+ *    during the call only.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream). Every call only enqueues work on it and returns; results are ready
  *    when the stream is synchronised.
@@ -94,7 +97,13 @@ typedef struct gdgs_gaussians {
 /* Pinhole camera (host struct, by value semantics). OpenCV axes: x right, y down,
  * z forward. world_to_cam is the row-major 3x4 matrix [W | t] whose 3x3 part is
  * the W of Eq. sig2d. Pixel (row i, column j) has its centre at x = j + 0.5,
- * y = i + 0.5. Gaussians with camera depth <= near_plane are culled. */
+ * y = i + 0.5. Gaussians with camera depth <= near_plane are culled.
+ * Depth precision: the camera depth t_z = W[2] . mean + t[2] is evaluated in
+ * float-float arithmetic (about 44 bits). The near cull compares it with
+ * near_plane, and the front-to-back order ("sorted from the view direction",
+ * Eq. color) follows it to 2^-31 relative: two Gaussians whose depths differ by
+ * more than that are composited in exact depth order; closer ones may come in
+ * either order; equal depths computed from equal terms keep ascending index. */
 typedef struct gdgs_camera {
   float world_to_cam[12];
   float fx, fy, cx, cy;
@@ -169,7 +178,7 @@ typedef struct gdgs_solve_stats {
 typedef struct gdgs_projected {
   float *mean2d;    /* [n][2] projected centre in pixels (x, y) */
   float *cov2d;     /* [n][3] Sigma2D incl. dilation: xx, xy, yy */
-  float *depth;     /* [n] camera-space z (0 if culled) */
+  float *depth;     /* [n] camera-space z rounded to float (0 if culled) */
   int32_t *rect;    /* [n][4] touched tiles x0, y0, x1, y1 (half open; empty if culled) */
 } gdgs_projected;
 
@@ -300,13 +309,20 @@ GDGS_API int gdgs_sync_status(const void *ws, gdgs_solve_stats *stats, void *str
  * library, held on every GPU that loads it until the process exits.
  *   Arguments as for gdgs_poisson_reconstruct; `stats` (host, nullable): when
  *   given, the call waits for `stream` and fills it (and returns the device
- *   status), otherwise it only enqueues.
+ *   status), otherwise it only enqueues. Waiting is not allowed while `stream`
+ *   is being captured: there `stats` must be NULL (a non-NULL `stats` returns
+ *   GDGS_ERR_INVALID_ARG with nothing enqueued), and the status of the replayed
+ *   solve is read afterwards with gdgs_poisson_static_status().
  *   Sizes whose workspace (gdgs_workspace_size(0, ...)) exceeds 32 MiB are
  *   rejected with GDGS_ERR_WORKSPACE before anything is enqueued; about
  *   640 x 480 x 3 or 1024 x 1024 x 1 fit.
- *   No cudaMalloc, cudaFree or other allocating call is made. The first call on
- *   a device looks the array's address up (cudaGetSymbolAddress) and should come
- *   before any stream capture on that device.
+ *   No cudaMalloc, cudaFree or other allocating call is made for the scratch.
+ *   The first call on a device looks the array's address up
+ *   (cudaGetSymbolAddress) and should come before any stream capture on that
+ *   device. Outside a capture, the first call for each image size and solver
+ *   option set also builds and instantiates the CUDA graph of its cycle loop
+ *   (driver objects, created once; GDGS_GRAPHS=0 in the environment runs the
+ *   cycles as plain launches and creates none).
  *   All calls share the one array, which keeps the last call's contents (what
  *   must start at zero is cleared by each call); calls that overlap on the GPU
  *   race and must be ordered by the caller (one stream, or synchronisation). */
@@ -314,6 +330,12 @@ GDGS_API int gdgs_poisson_reconstruct_static(const float *grad_maps, const uint8
                                              int32_t channels, int32_t height, int32_t width,
                                              const float *mean, const gdgs_solver_opts *sopts,
                                              float *image, gdgs_solve_stats *stats, void *stream);
+
+/* Wait for `stream`, then read the device status word and statistics of the last
+ * gdgs_poisson_reconstruct_static solve on the current device (for example one
+ * replayed from a captured graph). `stats` (host) may be NULL. Returns the device
+ * status, or GDGS_ERR_CUDA if the synchronisation failed. */
+GDGS_API int gdgs_poisson_static_status(gdgs_solve_stats *stats, void *stream);
 
 /* ---- diagnostics (host side; not needed on the render path) ---------------- */
 

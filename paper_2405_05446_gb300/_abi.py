@@ -109,6 +109,7 @@ PROTOTYPES = {
     "gdgs_poisson_reconstruct_static": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(_f),
                                                        ctypes.POINTER(SolverOpts), _p,
                                                        ctypes.POINTER(SolveStats), _p]),
+    "gdgs_poisson_static_status": (ctypes.c_int, [ctypes.POINTER(SolveStats), _p]),
     "gdgs_kernel_launch_count": (ctypes.c_uint64, []),
     "gdgs_profile_begin": (ctypes.c_int, []),
     "gdgs_profile_end": (ctypes.c_int, [ctypes.POINTER(KernelTime), _i32, ctypes.POINTER(_i32)]),

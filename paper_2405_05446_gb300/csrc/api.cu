@@ -105,6 +105,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
       p->off_pkey[b] = cv.take(4 * (size_t)p->pair_cap);
       p->off_pval[b] = cv.take(4 * (size_t)p->pair_cap);
     }
+    p->off_dlo = cv.take(4 * (size_t)n);
     p->off_hist = cv.take(4 * 256 * (size_t)(p->radix_blocks_max + 1));
     p->off_blocksum = cv.take(8 * (size_t)((n + kBinBlock - 1) / kBinBlock + 2));
     p->off_gtiles = cv.take(4 * (size_t)n);
@@ -211,6 +212,7 @@ ProjectArgs project_args(const gdgs_gaussians *g, const gdgs_camera *cam,
   a.smean = (float4 *)(ws + p.off_smean);
   a.sconic = (float4 *)(ws + p.off_sconic);
   a.key = (uint32_t *)(ws + p.off_dkey[0]);  // sorted in place by the depth sort
+  a.key_lo = (uint32_t *)(ws + p.off_dlo);
   a.rect = (uint2 *)(ws + p.off_rect);
   a.ctrl = (Ctrl *)(ws + p.off_ctrl);
   return a;
@@ -234,13 +236,13 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
   uint8_t *mk = mask ? mask : (uint8_t *)(ws + p.off_mask);
   const uint32_t *pval_sorted = (const uint32_t *)(ws + p.off_pval[0]);
   if (g->n > 0) {
-    // 1. depth order of the Gaussians (32-bit keys)
+    // 1. depth order of the Gaussians (float-float depth: lo digit, then hi bits)
     uint32_t *dk0 = (uint32_t *)(ws + p.off_dkey[0]), *dv0 = (uint32_t *)(ws + p.off_dval[0]);
     uint32_t *dk1 = (uint32_t *)(ws + p.off_dkey[1]), *dv1 = (uint32_t *)(ws + p.off_dval[1]);
     const int dblocks = (int)((g->n + kRadixBlockSmall - 1) / kRadixBlockSmall);
     bool alt = false;
-    e = radix_sort_pairs(dk0, dv0, dk1, dv1, true, nullptr, (unsigned)g->n, 32, hist,
-                         kRadixItemsSmall, dblocks, &alt, st);
+    e = radix_sort_pairs(dk0, dv0, dk1, dv1, true, (const uint32_t *)(ws + p.off_dlo), nullptr,
+                         (unsigned)g->n, 32, hist, kRadixItemsSmall, dblocks, &alt, st);
     if (e != cudaSuccess) return e;
     const uint32_t *order = alt ? dv1 : dv0;
     // 2. emit (tile, Gaussian) pairs in depth order
@@ -268,8 +270,8 @@ cudaError_t raster_path(const gdgs_gaussians *g, const gdgs_camera *cam,
     uint32_t *pk1 = (uint32_t *)(ws + p.off_pkey[1]), *pv1 = (uint32_t *)(ws + p.off_pval[1]);
     alt = false;
     const int pblocks = (int)(((int64_t)p.pair_cap + kRadixBlock - 1) / kRadixBlock);
-    e = radix_sort_pairs(pk0, pv0, pk1, pv1, false, &ctrl->n_pairs, p.pair_cap, tbits, hist,
-                         kRadixItems, pblocks, &alt, st);
+    e = radix_sort_pairs(pk0, pv0, pk1, pv1, false, nullptr, &ctrl->n_pairs, p.pair_cap, tbits,
+                         hist, kRadixItems, pblocks, &alt, st);
     if (e != cudaSuccess) return e;
     const uint32_t *pk_sorted = alt ? pk1 : pk0;
     pval_sorted = alt ? pv1 : pv0;

@@ -123,6 +123,7 @@ struct Plan {
   size_t off_ctrl;
   size_t off_smean, off_sconic, off_rect;              // projected splats [n]
   size_t off_dkey[2], off_dval[2];                     // depth sort [n]
+  size_t off_dlo;                                      // depth sort secondary key [n]
   size_t off_hist;                                     // radix histograms
   size_t off_blocksum;                                 // scan partials
   size_t off_gtiles;                                   // tiles per depth-ordered Gaussian
@@ -168,7 +169,8 @@ struct ProjectArgs {
   // outputs (workspace)
   float4 *smean;   // mx_hi, my_hi, mx_lo, my_lo
   float4 *sconic;  // conic * exp_coef * log2(e) (a, 2b, c), opacity
-  uint32_t *key;   // float bits of the depth key, kInvalidKey when culled
+  uint32_t *key;   // float bits of the depth's hi part, kInvalidKey when culled
+  uint32_t *key_lo;  // 8-bit digit of the depth's lo part in units of ulp(hi) / 256
   uint2 *rect;     // x0 | x1 << 16, y0 | y1 << 16 (tiles, half open)
   // optional outputs
   float *o_mean2d, *o_cov2d, *o_depth;
@@ -179,12 +181,13 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t st);
 
 // Stable LSD radix sort of 32-bit keys with 32-bit values over bits
 // [0, nbits). n = min(*n_dev, cap) if n_dev else cap. vals_in == nullptr means
-// the values are the element indices. Blocks of kRadixThreads * items keys
-// (items kRadixItems or kRadixItemsSmall), max_blocks of them at most; hist
-// holds 256 * (max_blocks + 1) words. Returns in *out_is_alt whether the
-// result sits in the alternate buffers.
+// the values are the element indices. lo_keys (nullable): a secondary key whose
+// low 8 bits order elements with equal keys (one extra pass, run first).
+// Blocks of kRadixThreads * items keys (items kRadixItems or kRadixItemsSmall),
+// max_blocks of them at most; hist holds 256 * (max_blocks + 1) words. Returns
+// in *out_is_alt whether the result sits in the alternate buffers.
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
-                             uint32_t *vals_alt, bool implicit_vals,
+                             uint32_t *vals_alt, bool implicit_vals, const uint32_t *lo_keys,
                              const unsigned long long *n_dev, unsigned cap, int nbits,
                              uint32_t *hist, int items, int max_blocks, bool *out_is_alt,
                              cudaStream_t st);

@@ -13,8 +13,11 @@
 // float-float arithmetic (about 44 bits) and stored as a (hi, lo) float pair. In FP32 the centre of a splat 1000 px from
 // the origin carries ~1e-4 px of rounding, which moves alpha by ~1e-4 relative;
 // the pair keeps the later per-pixel offset accurate to FP32 relative precision.
-// The view-depth sort key is the FP32 value fma(w20, x, fma(w21, y, fma(w22, z,
-// w23))) with single-rounding fmas, so the order is reproducible bit for bit.
+// The camera depth is a float-float pair (hi, lo) as well. The near cull compares
+// the pair with the near plane, and the view-depth sort orders by hi and then by
+// an 8-bit digit of lo in units of ulp(hi) / 256, so two depths are ordered as in
+// exact arithmetic whenever they differ by more than 2^-31 relative (an FP32 key
+// alone merges depths within 2^-24 and leaves their order to the index).
 #include <math.h>
 
 #include "gdgs_internal.cuh"
@@ -68,6 +71,18 @@ __device__ __forceinline__ FF ff_affine(const float *w, float x, float y, float 
   return ff_add(ff_add(ff_prod(w[0], x), ff_prod(w[1], y)), ff_add(ff_prod(w[2], z), FF{w[3], 0.f}));
 }
 
+// The 8-bit digit floor(lo / ulp(hi) * 256) + 128 of a normalised pair with
+// hi > 0 (|lo| <= ulp(hi) / 2, so the digit lies in [0, 256]; 256 is clamped).
+// For equal hi it is monotone in lo. The scaling by 2^(158 - e), e the biased
+// exponent of hi, is exact (ldexpf of a power of two), and |lo| 2^(158 - e)
+// <= 128. Very small depths (e < 31) get the middle digit.
+__device__ __forceinline__ uint32_t depth_lo_digit(FF t) {
+  const int e = (int)((__float_as_uint(t.hi) >> 23) & 0xffu);
+  if (e < 31 || e == 255) return 128u;
+  const float q = floorf(ldexpf(t.lo, 158 - e)) + 128.f;
+  return (uint32_t)fminf(fmaxf(q, 0.f), 255.f);
+}
+
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   griddep_enter();
   if (a.cam_dev) {  // camera from device memory (a graph replays for any camera)
@@ -96,9 +111,11 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
     for (int q = 0; q < a.Q; ++q) finite = finite && isfinite(a.grad[i * a.Q + q]);
     if (!finite) set_status(a.ctrl, GDGS_ERR_NONFINITE);
 
-    float key = __fmaf_rn(a.w2c[8], mx, __fmaf_rn(a.w2c[9], my, __fmaf_rn(a.w2c[10], mz, a.w2c[11])));
+    // camera depth t_z as a float-float pair; culled unless t_z > near
+    const FF t2 = ff_affine(a.w2c + 8, mx, my, mz);
+    const bool in_front = t2.hi > a.znear || (t2.hi == a.znear && t2.lo > 0.f);
     const float qn = qw * qw + qx * qx + qy * qy + qz * qz;
-    bool ok = finite && qn > 1e-20f && key > a.znear && opa >= a.alpha_min;
+    bool ok = finite && qn > 1e-20f && in_front && opa >= a.alpha_min;
 
     float u_f = 0.f, v_f = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
     int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
@@ -125,7 +142,6 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 
       // camera-space centre and projected centre in float-float
       const FF t0 = ff_affine(a.w2c, mx, my, mz), t1 = ff_affine(a.w2c + 4, mx, my, mz);
-      const FF t2 = ff_affine(a.w2c + 8, mx, my, mz);
       const FF u = ff_add(ff_mul(ff_div(t0, t2), a.fx), FF{a.cx, 0.f});
       const FF v = ff_add(ff_mul(ff_div(t1, t2), a.fy), FF{a.cy, 0.f});
       const float u_hi = u.hi, v_hi = v.hi, u_lo = u.lo, v_lo = v.lo;
@@ -183,7 +199,9 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
       }
     }
     if (!visible) { tx0 = tx1 = ty0 = ty1 = 0; }
+    const float key = t2.hi;
     a.key[i] = visible ? __float_as_uint(key) : kInvalidKey;
+    a.key_lo[i] = visible ? depth_lo_digit(t2) : 0u;
     a.rect[i] = make_uint2((unsigned)tx0 | ((unsigned)tx1 << 16), (unsigned)ty0 | ((unsigned)ty1 << 16));
     if (a.o_mean2d) {
       a.o_mean2d[2 * i] = visible ? u_f : 0.f;

@@ -2,7 +2,11 @@
 //
 // The composite of Eq. color / Eq. gdgs2d visits splats "sorted from the view
 // direction". The path orders them in two stable sorts instead of one wide key:
-//   1. sort the Gaussians by their FP32 depth key (32-bit keys, N items);
+//   1. sort the Gaussians by their camera depth, held as a float-float pair
+//      (hi, lo): one pass over an 8-bit digit of lo in units of ulp(hi) / 256,
+//      then four passes over the float bits of hi (positive floats sort as
+//      unsigned integers). Pairs with equal hi are thereby ordered by lo, which
+//      resolves the depth to 2^-31 relative instead of float32's 2^-24 (N items);
 //   2. walk them in that order, emit one (tile, Gaussian) pair per touched tile,
 //      so pairs come out depth-ordered;
 //   3. stable-sort the pairs by tile id only (ceil(log2 T) bits, 2 passes at
@@ -109,11 +113,15 @@ __global__ void __launch_bounds__(256) radix_scan_top_kernel(uint32_t *tot, unsi
   if (threadIdx.x < ndig) tot[threadIdx.x] = ex;
 }
 
+// keys_next (nullable): the key written out for element i is keys_next[i]
+// instead of the key ranked on, so a first pass over a secondary key leaves the
+// primary keys in its order for the passes that follow.
 template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                      uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
-                     unsigned mask, const uint32_t *hist, const uint32_t *dbase) {
+                     unsigned mask, const uint32_t *hist, const uint32_t *dbase,
+                     const uint32_t *keys_next) {
   griddep_enter();
   constexpr int kWarps = kRadixThreads / 32;
   __shared__ unsigned run[256];
@@ -150,7 +158,7 @@ radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t 
     __syncthreads();
     if (valid) {
       const unsigned pos = wcnt[w][d] + rank;
-      keys_out[pos] = key;
+      keys_out[pos] = keys_next ? keys_next[i] : key;
       vals_out[pos] = val;
     }
     __syncthreads();
@@ -384,27 +392,50 @@ ranges_kernel(const uint32_t *keys, Ctrl *ctrl, unsigned cap, uint2 *range, uint
 }  // namespace
 
 template <int ITEMS>
+cudaError_t radix_pass(const uint32_t *ki, const uint32_t *vi, uint32_t *ko, uint32_t *vo,
+                       const uint32_t *knext, const unsigned long long *n_dev, unsigned cap,
+                       int shift, unsigned mask, uint32_t *hist, unsigned blocks,
+                       cudaStream_t st) {
+  { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
+  uint32_t *dtot = hist + (size_t)256 * blocks;
+  { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel<ITEMS>, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
+  { LaunchScope ls_("radix_scan_top", st); launch_k(radix_scan_top_kernel, 1, 256, 0, st, dtot, mask + 1); }
+  {
+    LaunchScope ls_("radix_scatter", st);
+    launch_k(radix_scatter_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, vi, ko, vo, n_dev, cap,
+             shift, mask, (const uint32_t *)hist, (const uint32_t *)dtot, knext);
+  }
+  return cudaGetLastError();
+}
+
+template <int ITEMS>
 cudaError_t radix_sort_t(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                         bool implicit_vals, const unsigned long long *n_dev, unsigned cap,
-                         int nbits, uint32_t *hist, int max_blocks, bool *out_is_alt,
-                         cudaStream_t st) {
+                         bool implicit_vals, const uint32_t *lo_keys,
+                         const unsigned long long *n_dev, unsigned cap, int nbits,
+                         uint32_t *hist, int max_blocks, bool *out_is_alt, cudaStream_t st) {
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   bool alt = false;
   bool first = true;
   const unsigned blocks = (unsigned)max_blocks;
+  if (blocks == 0) {
+    *out_is_alt = false;
+    return cudaSuccess;
+  }
+  if (lo_keys) {  // secondary key first (LSD): its low 8 bits, carrying the primary keys
+    cudaError_t e = radix_pass<ITEMS>(lo_keys, implicit_vals ? nullptr : vi, ko, vo, ki, n_dev,
+                                      cap, 0, 0xffu, hist, blocks, st);
+    if (e != cudaSuccess) return e;
+    first = false;
+    uint32_t *t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    alt = !alt;
+  }
   for (int shift = 0; shift < nbits; shift += 8) {
     const int bits = nbits - shift < 8 ? nbits - shift : 8;
     const unsigned mask = (1u << bits) - 1u;
-    if (blocks == 0) break;
-    { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
-    uint32_t *dtot = hist + (size_t)256 * max_blocks;
-    { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel<ITEMS>, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
-    { LaunchScope ls_("radix_scan_top", st); launch_k(radix_scan_top_kernel, 1, 256, 0, st, dtot, mask + 1); }
-    {
-      LaunchScope ls_("radix_scatter", st);
-      launch_k(radix_scatter_kernel<ITEMS>, blocks, kRadixThreads, 0, st,
-          ki, (first && implicit_vals) ? nullptr : vi, ko, vo, n_dev, cap, shift, mask, hist, dtot);
-    }
+    cudaError_t e = radix_pass<ITEMS>(ki, (first && implicit_vals) ? nullptr : vi, ko, vo, nullptr,
+                                      n_dev, cap, shift, mask, hist, blocks, st);
+    if (e != cudaSuccess) return e;
     first = false;
     uint32_t *t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -415,16 +446,16 @@ cudaError_t radix_sort_t(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uin
 }
 
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
-                             uint32_t *vals_alt, bool implicit_vals,
+                             uint32_t *vals_alt, bool implicit_vals, const uint32_t *lo_keys,
                              const unsigned long long *n_dev, unsigned cap, int nbits,
                              uint32_t *hist, int items, int max_blocks, bool *out_is_alt,
                              cudaStream_t st) {
   if (items == kRadixItemsSmall)
-    return radix_sort_t<kRadixItemsSmall>(keys, vals, keys_alt, vals_alt, implicit_vals, n_dev,
-                                          cap, nbits, hist, max_blocks, out_is_alt, st);
+    return radix_sort_t<kRadixItemsSmall>(keys, vals, keys_alt, vals_alt, implicit_vals, lo_keys,
+                                          n_dev, cap, nbits, hist, max_blocks, out_is_alt, st);
   if (items == kRadixItems)
-    return radix_sort_t<kRadixItems>(keys, vals, keys_alt, vals_alt, implicit_vals, n_dev, cap,
-                                     nbits, hist, max_blocks, out_is_alt, st);
+    return radix_sort_t<kRadixItems>(keys, vals, keys_alt, vals_alt, implicit_vals, lo_keys, n_dev,
+                                     cap, nbits, hist, max_blocks, out_is_alt, st);
   return cudaErrorInvalidValue;
 }
 

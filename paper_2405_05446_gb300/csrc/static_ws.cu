@@ -50,11 +50,28 @@ extern "C" int gdgs_poisson_reconstruct_static(const float *grad_maps, const uin
   const size_t need = gdgs_workspace_size(0, channels, width, height, nullptr, sopts);
   if (need == 0) return GDGS_ERR_INVALID_ARG;
   if (need > kStaticBytes) return GDGS_ERR_WORKSPACE;  // larger than the fixed scratch
+  if (stats) {
+    // filling stats waits for the stream, which a stream capture does not allow:
+    // refuse before anything is enqueued rather than invalidate the capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return GDGS_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return GDGS_ERR_INVALID_ARG;
+  }
   void *ws = nullptr;
   int s = static_workspace(&ws);
   if (s != GDGS_OK) return s;
   s = gdgs_poisson_reconstruct(grad_maps, tile_mask, channels, height, width, mean, sopts, image,
                                ws, kStaticBytes, stream);
   if (s != GDGS_OK || !stats) return s;
+  return gdgs_sync_status(ws, stats, stream);
+}
+
+extern "C" int gdgs_poisson_static_status(gdgs_solve_stats *stats, void *stream) {
+  void *ws = nullptr;
+  const int s = static_workspace(&ws);
+  if (s != GDGS_OK) return s;
   return gdgs_sync_status(ws, stats, stream);
 }

@@ -2,9 +2,13 @@
 through the C ABI, and compare with the FP64 oracle under the stated tolerances.
 
 Tolerances (floating point):
-  gradient maps  max |gpu - oracle| over non-ambiguous pixels <= 1e-5 * max |oracle|
-  image          max |gpu - oracle| <= 1e-3 * max(1, oracle max - oracle min),
-                 i.e. 1e-3 on a [0, 1] scale after mapping the image range onto it
+  gradient maps  max |gpu - oracle| over non-ambiguous pixels <= 1e-5 * max |oracle|;
+                 ambiguous pixels (a decision within its float32 error bound of the
+                 threshold, see oracle_raster.c) are at most AMB_FRAC_MAX of all pixels
+  image          max |gpu - oracle| <= 1e-3 absolute for rendered views (images near
+                 [0, 1]); for solver tests on synthetic fields of arbitrary scale, and
+                 for Laplacian-attribute views (whose least-squares images span
+                 hundreds), 1e-3 after mapping the oracle image's range onto [0, 1]
 """
 import numpy as np
 import torch
@@ -15,7 +19,11 @@ from paper_2405_05446_gb300 import build as B
 
 MAP_TOL = 1e-5
 IMG_TOL = 1e-3
+# measured with the oracle's float32 error model: 6.3e-4 of the 1080p workload's pixels
 AMB_FRAC_MAX = 1e-3
+# The library orders Gaussians by a float-float camera depth resolved to 2^-31 relative
+# (include/gdgs.h, gdgs_camera); the oracle flags depth ties within 4x that.
+LIB_DEPTH_REL = 2.0 ** -29
 
 
 def ensure_lib():
@@ -30,6 +38,13 @@ def oracle_opts(ro) -> O.RasterOpts:
     return O.RasterOpts(alpha_min=float(np.float32(ro.alpha_min)), alpha_max=float(np.float32(ro.alpha_max)),
                         t_min=float(np.float32(ro.t_min)), dilation=float(np.float32(ro.dilation)),
                         exp_coef=float(np.float32(ro.exp_coef)))
+
+
+def oracle_maps(scene, cam, ro=None, **kw):
+    """The oracle's composite for the options `ro` the kernel receives, with the depth
+    ties flagged at the library's stated depth precision."""
+    return O.render_gradients(scene, cam, oracle_opts(ro or G.raster_opts()),
+                              depth_rel=LIB_DEPTH_REL, **kw)
 
 
 def gpu_maps(scene, cam, ropts=None, with_mask=False):

@@ -111,3 +111,39 @@ def test_autograd_function_and_descent():
         opt.step()
         losses.append(float(loss))
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_autograd_raises_on_device_errors():
+    """The binding reads both solves' statuses: a forward that did not converge in its
+    cycle budget raises at backward, and so does an adjoint solve that did not."""
+    from paper_2405_05446_gb300 import autograd as A
+    sc, cam = _scene64(4)
+    mean = [0.5, 0.5, 0.5]
+    ropts = G.raster_opts(pairs_per_gaussian=64, **SMOOTH)
+    one_cycle = G.solver_opts(max_cycles=1, rtol=1e-7)
+
+    def params_of(scene):
+        return [torch.tensor(np.asarray(getattr(scene, k)), device="cuda", requires_grad=True)
+                for k in D.PARAMS]
+
+    # forward: one V-cycle cannot reach 1e-7 on this view
+    params = params_of(sc)
+    img = A.render_view(*params, cam, mean, ropts, one_cycle)
+    w = torch.randn_like(img)
+    with pytest.raises(G.GDGSError) as ei:
+        (img * w).sum().backward()
+    assert ei.value.code == G._abi.ERR_NO_CONVERGE
+    # adjoint only: every Gaussian behind the camera gives rho = 0, which the forward
+    # solves at once; the adjoint of a random d image needs more than one cycle
+    behind = S.Scene(sc.mean - np.float32([0.0, 0.0, 10.0]), sc.scale, sc.quat, sc.opacity, sc.grad)
+    params = params_of(behind)
+    img = A.render_view(*params, cam, mean, ropts, one_cycle)
+    torch.cuda.synchronize()
+    assert torch.allclose(img, torch.full_like(img, 0.5))
+    with pytest.raises(G.GDGSError) as ei:
+        (img * w).sum().backward()
+    assert ei.value.code == G._abi.ERR_NO_CONVERGE
+    # with the check off the same call returns (unchecked) gradients
+    img = A.render_view(*params, cam, mean, ropts, one_cycle, check_status=False)
+    (img * w).sum().backward()
+    assert all(p.grad is not None for p in params)

@@ -7,8 +7,8 @@ import oracle as O
 import paper_2405_05446_gb300 as G
 from paper_2405_05446_gb300 import scenes as S
 
-from gpu_util import (AMB_FRAC_MAX, IMG_TOL, MAP_TOL, ensure_lib, gpu_maps, gpu_poisson,
-                      img_err, map_rel_err, oracle_opts)
+from gpu_util import (AMB_FRAC_MAX, IMG_TOL, LIB_DEPTH_REL, MAP_TOL, ensure_lib, gpu_maps,
+                      gpu_poisson, img_err, map_rel_err, oracle_maps, oracle_opts)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,12 +38,18 @@ def test_projection_matches_oracle():
     G.project(g, cam, ws, ro, m2, cv, dp, rc)
     st = G.sync_status(ws)
     assert st["status"] == 0
-    proj = O.project(scene, cam, oracle_opts(ro))
+    proj = O.project(scene, cam, oracle_opts(ro), depth_rel=LIB_DEPTH_REL)
     vis = rc[:, 2].cpu().numpy() > rc[:, 0].cpu().numpy()
-    # the depth key decides the order: identical bits on both sides
     ok = proj[:, O.VALID] > 0
-    np.testing.assert_array_equal(dp.cpu().numpy()[vis], proj[vis, O.KEY].astype(np.float32))
-    assert not np.any(vis & ~ok)
+    # the returned depth is the float-float camera depth rounded to float: within
+    # half an ulp of the FP64 depth, plus the pair's own error (2^-44 of its terms)
+    dpn = dp.cpu().numpy().astype(np.float64)
+    t = proj[vis, O.DEPTH]
+    half_ulp = np.spacing(np.float32(t)).astype(np.float64) / 2
+    assert np.all(np.abs(dpn[vis] - t) <= half_ulp + 2.0 ** -44 * 8 * np.abs(t))
+    # the near cull agrees with the FP64 depth except within the depth bound
+    sure = proj[:, O.NEARAMB] == 0
+    assert not np.any(vis & ~ok & sure)
     m2 = m2.cpu().numpy().astype(np.float64)
     np.testing.assert_allclose(m2[vis, 0], proj[vis, O.MX], atol=1e-4, rtol=0)
     np.testing.assert_allclose(m2[vis, 1], proj[vis, O.MY], atol=1e-4, rtol=0)
@@ -73,7 +79,7 @@ def test_gradient_maps_tiny(channels):
     cam = S.tiny_camera()
     gm, _, st = gpu_maps(scene, cam)
     assert st["status"] == 0
-    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    om, amb = oracle_maps(scene, cam)
     assert amb.mean() <= AMB_FRAC_MAX
     assert map_rel_err(gm, om, amb) <= MAP_TOL
 
@@ -82,7 +88,7 @@ def test_gradient_maps_ragged_prims_several_tiles():
     scene, cam = _small_prims()
     gm, _, st = gpu_maps(scene, cam)
     assert st["status"] == 0 and st["n_pairs"] > 0
-    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    om, amb = oracle_maps(scene, cam)
     assert amb.mean() <= AMB_FRAC_MAX
     assert map_rel_err(gm, om, amb) <= MAP_TOL
 
@@ -92,7 +98,7 @@ def test_gradient_maps_half_exponent_option():
     cam = S.tiny_camera(80, 48)
     ro = G.raster_opts(exp_coef=0.5, dilation=0.1)
     gm, _, st = gpu_maps(scene, cam, ro)
-    om, amb = O.render_gradients(scene, cam, oracle_opts(ro))
+    om, amb = oracle_maps(scene, cam, ro)
     assert map_rel_err(gm, om, amb) <= MAP_TOL
 
 
@@ -100,7 +106,7 @@ def test_tile_mask_and_untouched_tiles():
     scene = S.tiny_scene(1, n=60)  # sparse: most tiles empty
     cam = S.tiny_camera(100, 70)
     gm, mask, st = gpu_maps(scene, cam, with_mask=True)
-    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    om, amb = oracle_maps(scene, cam)
     H, W = cam.height, cam.width
     pix_mask = np.kron(mask, np.ones((16, 16), np.uint8))[:H, :W].astype(bool)
     # every pixel the oracle sees non-zero lies in an active tile
@@ -113,20 +119,19 @@ def test_tile_mask_and_untouched_tiles():
     assert st["n_active_tiles"] == int(mask.sum()) < mask.size
 
 
-def test_gradient_maps_1080p_sampled_pixels():
+def test_gradient_maps_1080p_whole_image():
+    """Every pixel of the 1920x1080 workload's six gradient planes against the oracle."""
     scene, cam, _, _ = S.workload("prims1080p")
     gm, _, st = gpu_maps(scene, cam)
     assert st["status"] == 0
-    rng = np.random.default_rng(0)
-    H, W = cam.height, cam.width
-    pix = np.concatenate([rng.integers(0, H * W, 3000), [0, W - 1, (H - 1) * W, H * W - 1]])
-    out, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()), pixels=pix)
-    i, j = pix // W, pix % W
-    got = gm[:, :, i, j].transpose(2, 0, 1)
-    ok = amb == 0
-    ref = np.abs(out).max()
-    assert np.abs(got[ok] - out[ok]).max() <= MAP_TOL * ref
-    assert amb.mean() <= 5 * AMB_FRAC_MAX
+    om, amb = oracle_maps(scene, cam)
+    print(f"1080p maps: {int(amb.sum())} ambiguous pixels ({amb.mean():.2e}), "
+          f"max rel err {map_rel_err(gm, om, amb):.2e}")
+    assert amb.mean() <= AMB_FRAC_MAX
+    assert map_rel_err(gm, om, amb) <= MAP_TOL
+    # ambiguous pixels differ by at most one decision's worth of a splat's attribute
+    d = np.abs(gm - om)[:, :, amb > 0]
+    assert d.size == 0 or d.max() <= 2 * np.abs(scene.grad).max()
 
 
 def test_raster_deterministic():
@@ -360,7 +365,8 @@ def test_render_view_1080p_matches_oracle():
     ref, _, amb = O.render_view(scene, cam, mean, oracle_opts(G.raster_opts()))
     assert st["status"] == 0 and st["rel_residual"] <= rtol, st
     rel, absolute = img_err(img, ref)
-    assert rel <= IMG_TOL, (rel, absolute)
+    print(f"1080p view: max |gpu - oracle| = {absolute:.2e}, ambiguous pixels {int(amb.sum())}")
+    assert absolute <= IMG_TOL, (rel, absolute)
     assert st["n_visible"] > 0.9 * scene.n
 
 
@@ -547,7 +553,7 @@ def test_laplacian_field_matches_oracle():
     scene = S.with_laplacian_attribute(S.tiny_scene(2))
     cam = S.tiny_camera(96, 64)
     gm, _, st = gpu_maps(scene, cam)
-    om, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+    om, amb = oracle_maps(scene, cam)
     assert st["status"] == 0 and gm.shape == om.shape == (3, 64, 96)
     ok = amb == 0
     assert np.abs(gm - om)[:, ok].max() <= MAP_TOL * np.abs(om).max()
@@ -575,7 +581,7 @@ def test_render_view_laplacian_with_threshold(t):
     scene = S.with_laplacian_attribute(scene)
     mean = [0.5, 0.4, 0.6]
     if t > 0:
-        rho, amb = O.render_gradients(scene, cam, oracle_opts(G.raster_opts()))
+        rho, amb = oracle_maps(scene, cam)
         t = _well_posed_threshold(scene, rho, amb, [t * (1 + 0.005 * i) for i in range(400)])
         assert t is not None
         assert 0.2 < (np.abs(rho) < t).mean() < 0.9  # the threshold removes a real share
