@@ -115,8 +115,31 @@ def mg_levels(H: int, W: int, coarse_max: int = 8):
 
 
 def algorithmic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,
+                      n_pairs: int, nu1: int = 2, nu2: int = 1) -> float:
+    """Algorithmic bytes per view: the per-unit figures of the survey's byte model
+    (one smoother sweep 12 B per unknown - read u and f, write u; fused residual and
+    restriction 9 B; prolongation and correction 9 B; the per-pixel passes one read
+    of their inputs and one write of their outputs) times the units one view
+    processes. A fused kernel moves less than this (see min_traffic_bytes)."""
+    px = C * H * W
+    lv, t = mg_levels(H, W)
+    down, up = 12 * nu1 + 9, 12 * nu2 + 9  # per unknown and cycle
+    if kernel == "mg0_down":
+        return cycles * px * down
+    if kernel == "mg0_up":
+        return cycles * px * up
+    if kernel in ("mg_down", "mg_up"):  # levels 1 .. t-1
+        per = down if kernel == "mg_down" else up
+        return cycles * sum(per * C * h * w for h, w in lv[1:t])
+    if kernel == "mg_tail":    # levels t .. coarsest, and the FP64 coarse inverse
+        nc = lv[-1][0] * lv[-1][1]
+        return cycles * C * (sum((down + up) * h * w for h, w in lv[t:-1]) + 8 * nc * nc)
+    return min_traffic_bytes(kernel, C, H, W, cycles, n_gauss, n_pairs)
+
+
+def min_traffic_bytes(kernel: str, C: int, H: int, W: int, cycles: int, n_gauss: int,
                       n_pairs: int) -> float:
-    """Bytes each kernel must move per view (one pass over its inputs and outputs)."""
+    """Bytes each fused kernel must move per view (one pass over its inputs and outputs)."""
     px = C * H * W
     lv, t = mg_levels(H, W)
     if kernel == "mg0_down":   # r_k in; e, coarse rhs out
@@ -543,15 +566,19 @@ def main():
     kernels = {k: {"launches_per_view": n / nv, "ms_per_view": ms / nv,
                    "share": ms / tot if tot else 0.0} for k, (n, ms) in sorted(
         prof.items(), key=lambda kv: -kv[1][1])}
+    nus = dict(nu1=sopts.nu1, nu2=sopts.nu2)
     hbm_kernels = [k for k in kernels if algorithmic_bytes(k, C, H, W, st["cycles"], scene.n,
-                                                            st["n_pairs"]) > 0 and k != "raster"]
+                                                            st["n_pairs"], **nus) > 0 and k != "raster"]
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     roof_k = dom if dom in hbm_kernels else max(hbm_kernels, key=lambda k: kernels[k]["share"])
-    per_kernel_roof = {}
+    per_kernel_roof, per_kernel_min = {}, {}
     for k in hbm_kernels:
-        b_ = algorithmic_bytes(k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
-        per_kernel_roof[k] = round(b_ / (kernels[k]["ms_per_view"] / 1e3) / 1e9 / hbm, 4)
-    nbytes = algorithmic_bytes(roof_k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
+        sec = kernels[k]["ms_per_view"] / 1e3
+        b_ = algorithmic_bytes(k, C, H, W, st["cycles"], scene.n, st["n_pairs"], **nus)
+        per_kernel_roof[k] = round(b_ / sec / 1e9 / hbm, 4)
+        m_ = min_traffic_bytes(k, C, H, W, st["cycles"], scene.n, st["n_pairs"])
+        per_kernel_min[k] = round(m_ / sec / 1e9 / hbm, 4)
+    nbytes = algorithmic_bytes(roof_k, C, H, W, st["cycles"], scene.n, st["n_pairs"], **nus)
     ms = kernels[roof_k]["ms_per_view"]
     launches_pv = kernels[roof_k]["launches_per_view"]
     achieved = nbytes / (ms / 1e3) / 1e9
@@ -564,7 +591,10 @@ def main():
                 "traffic_source": tr,
                 "algorithmic_bytes_per_view": nbytes,
                 "dominant_kernel": dom, "dominant_share": kernels[dom]["share"],
-                "frac_by_kernel": per_kernel_roof}
+                "frac_by_kernel": per_kernel_roof,
+                "bytes_model": "per unknown and cycle: 12 B per smoother sweep, 9 B residual + "
+                               "restriction, 9 B prolongation + correction",
+                "frac_by_kernel_min_traffic": per_kernel_min}
 
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,

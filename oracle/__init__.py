@@ -90,8 +90,11 @@ def _f32(a):
 
 
 def camera_array(cam) -> np.ndarray:
-    w = np.asarray(cam.world_to_cam, dtype=np.float64).reshape(12)
-    return np.concatenate([w, [cam.fx, cam.fy, cam.cx, cam.cy, cam.near]]).astype(np.float64)
+    """The camera as the float32 values the C ABI's gdgs_camera carries (pose,
+    intrinsics, near plane), promoted to float64 like every other input."""
+    w = np.asarray(cam.world_to_cam, dtype=np.float32).reshape(12)
+    intr = np.array([cam.fx, cam.fy, cam.cx, cam.cy, cam.near], dtype=np.float32)
+    return np.concatenate([w, intr]).astype(np.float64)
 
 
 # relative precision of a plain float32 evaluation of the depth w20 x + w21 y + w22 z + w23

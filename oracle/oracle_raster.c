@@ -67,15 +67,21 @@ enum {
  *    since d(Sigma^-1) = -Sigma^-1 dSigma Sigma^-1, the form moves by at most
  *    ||dSigma|| |Sigma^-1 d|^2. Along the major axis of an elongated splat this
  *    is u p, along the minor axis u p kappa.
- *  - the float32 form A dx^2 + 2B dx dy + C dy^2 itself: 3u times the sum of the
- *    magnitudes of its terms (large where the terms cancel);
- *  - the offset d from the pixel centre to the projected centre and the scaling
- *    of the form: C_P u max(p, 1).
+ *  - the float32 form A dx^2 + 2B dx dy + C dy^2 itself: C_F u times the sum of
+ *    the magnitudes of its terms (large where the terms cancel);
+ *  - the offset d from the pixel centre to the projected centre, rounded to
+ *    float32 once per coordinate (|dd| <= u |d|): the form moves by
+ *    2 |Sigma^-1 d| |dd|, so C_D u |Sigma^-1 d| |d|;
+ *  - the exponent's own rounding and its scaling: C_P u max(p, 1).
  * A further C_EXP u (relative) covers the exponential, to a few ulp, and the
- * product with the opacity. An absolute error e in p moves alpha by e of itself,
- * so the relative alpha error is the sum. err_scale multiplies it (1 by default;
- * 0 turns the ambiguity flags off). */
+ * opacity's log or product. An absolute error e in p moves alpha by e of
+ * itself, so the relative alpha error is the sum. An evaluation that rounds
+ * the projected centre itself to float32 (an offset error of u times the pixel
+ * coordinate, ~1e-4 px at x ~ 1000) is not covered. err_scale multiplies the
+ * whole bound (1 by default; 0 turns the ambiguity flags off). */
 #define ORC_C_SIGMA 16.0
+#define ORC_C_F 3.0
+#define ORC_C_D 4.0
 #define ORC_C_P 8.0
 #define ORC_C_EXP 8.0
 
@@ -86,16 +92,18 @@ static double alpha_err_at(const double *r, double dx, double dy, double kexp,
   double lmax = r[ORC_LMAX];
   double form_abs = fabs(r[ORC_CA]) * dx * dx + 2.0 * fabs(r[ORC_CB] * dx * dy) +
                     fabs(r[ORC_CC]) * dy * dy;
-  double ep = kexp * (ORC_C_SIGMA * lmax * (cdx * cdx + cdy * cdy) + 3.0 * form_abs) +
+  double cd = sqrt(cdx * cdx + cdy * cdy), dd = sqrt(dx * dx + dy * dy);
+  double ep = kexp * (ORC_C_SIGMA * lmax * cd * cd + ORC_C_F * form_abs + ORC_C_D * cd * dd) +
               ORC_C_P * fmax(p, 1.0);
   return err_scale * ORC_U * (ep + ORC_C_EXP);
 }
 
 /* The largest relative alpha error on the alpha_min level of a Gaussian whose
- * exponent there is lev (minor-axis direction; form terms at most kappa lev). */
+ * exponent there is lev (minor-axis direction; the form's terms and the offset
+ * term at most 2 kappa lev each). */
 static double alpha_err_max(double lev, double kappa) {
-  return ORC_U * ((ORC_C_SIGMA + 6.0) * kappa * fmax(lev, 1.0) + ORC_C_P * fmax(lev, 1.0) +
-                  ORC_C_EXP);
+  return ORC_U * ((ORC_C_SIGMA + 2.0 * ORC_C_F + 2.0 * ORC_C_D) * kappa * fmax(lev, 1.0) +
+                  ORC_C_P * fmax(lev, 1.0) + ORC_C_EXP);
 }
 
 /* cam: w2c[12] (row-major 3x4), fx, fy, cx, cy, near  -> 17 doubles

@@ -74,8 +74,10 @@ __device__ __forceinline__ void warp_sum(float (&v)[N]) {
 template <int Q>
 __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
   griddep_enter();
-  __shared__ float4 s_geo[256];   // mx, my (tile-relative), A, B
-  __shared__ float4 s_geo2[256];  // C, opacity, exponent limit, -
+  __shared__ float4 s_geo[256];   // as the forward rasteriser (StagedSplat)
+  __shared__ float4 s_geo2[256];
+  __shared__ float2 s_l[256];     // the centre's remainder l (offsets dx = X - l_x, ...)
+  __shared__ float s_opa[256];
   __shared__ float s_g[Q][256];
   __shared__ uint32_t s_id[256];
   __shared__ int s_last;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
   const float x0f = (float)x0, y0f = (float)y0;
   const uint2 rg = a.range[tile];
   const float amin = a.alpha_min, amax = a.alpha_max, tmin = a.t_min;
+  const float cut = log2f(amin) - 1e-3f;
   const size_t plane = (size_t)a.H * a.W;
   const size_t po = (size_t)py * a.W + px;
   if (threadIdx.x == 0) s_last = -1;
@@ -99,10 +102,12 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
     const unsigned j = s + threadIdx.x;
     if (j < rg.y) {
       const uint32_t g = a.pval[j];
-      const float4 m = a.smean[g];
       const float4 k = a.sconic[g];
-      s_geo[threadIdx.x] = make_float4((m.x - x0f) + m.z, (m.y - y0f) + m.w, k.x, k.y);
-      s_geo2[threadIdx.x] = make_float4(k.z, k.w, log2f(k.w / amin) + 1e-3f, 0.f);
+      const StagedSplat st = stage_splat(a.smean[g], k, x0f, y0f);
+      s_geo[threadIdx.x] = st.geo;
+      s_geo2[threadIdx.x] = st.geo2;
+      s_l[threadIdx.x] = make_float2(st.lx, st.ly);
+      s_opa[threadIdx.x] = k.w;
       s_id[threadIdx.x] = g;
 #pragma unroll
       for (int q = 0; q < Q; ++q) s_g[q][threadIdx.x] = a.attr[(size_t)g * Q + q];
@@ -122,10 +127,10 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
       for (int k = 0; k < cnt; ++k) {
         const float4 ge = s_geo[k];
         const float4 ge2 = s_geo2[k];
-        const float dx = fpx - ge.x, dy = fpy - ge.y;
-        const float p2 = dx * fmaf(ge.z, dx, ge.w * dy) + ge2.x * dy * dy;
-        if (p2 > ge2.z) continue;
-        const float al = fminf(amax, ge2.y * ex2_approx_b(-p2));
+        float X, Y;
+        const float t = ge2.y - staged_exponent(ge, ge2, fpx, fpy, X, Y);
+        if (t < cut) continue;
+        const float al = fminf(amax, ex2_approx_b(t));
         if (al < amin) continue;
         T = __fsub_rn(T, __fmul_rn(al, T));  // exactly as the forward rasteriser
         last = (int)(s + k);
@@ -165,11 +170,10 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
       if (inside && j <= last) {
         const float4 ge = s_geo[k];
         const float4 ge2 = s_geo2[k];
-        const float dx = fpx - ge.x, dy = fpy - ge.y;
-        const float p2 = dx * fmaf(ge.z, dx, ge.w * dy) + ge2.x * dy * dy;
-        if (p2 <= ge2.z) {
-          const float G = ex2_approx_b(-p2);
-          const float araw = ge2.y * G;
+        float X, Y;
+        const float t = ge2.y - staged_exponent(ge, ge2, fpx, fpy, X, Y);
+        if (t >= cut) {
+          const float araw = ex2_approx_b(t);  // opacity 2^-p2
           const float al = fminf(amax, araw);
           if (al >= amin) {
             const float Tb = T / (1.f - al);
@@ -182,13 +186,15 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
               B[q] = fmaf(c, al, (1.f - al) * B[q]);
             }
             if (araw < amax) {  // not clamped: the opacity and the exponent move a
-              const float gp = -dal * ge2.y * G * 0.6931471805599453f;  // d loss / d p2
+              const float gp = -dal * araw * 0.6931471805599453f;  // d loss / d p2
+              const float2 l = s_l[k];
+              const float dx = X - l.x, dy = Y - l.y;
               v[0] = -gp * (2.f * ge.z * dx + ge.w * dy);
               v[1] = -gp * (ge.w * dx + 2.f * ge2.x * dy);
               v[2] = gp * dx * dx;
               v[3] = gp * dx * dy;
               v[4] = gp * dy * dy;
-              v[5] = dal * G;
+              v[5] = dal * (araw / s_opa[k]);  // d alpha / d opacity = 2^-p2
             }
             T = Tb;
             any = true;

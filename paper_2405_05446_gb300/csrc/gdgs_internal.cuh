@@ -211,6 +211,54 @@ cudaError_t launch_tile_ranges(const uint32_t *sorted_keys, Ctrl *ctrl, unsigned
                                int T, uint2 *range, uint32_t *active, uint8_t *mask,
                                cudaStream_t st);
 
+// A projected splat staged for the 16x16 tile whose origin is (x0, y0), as the
+// forward and the backward rasteriser both evaluate it (the backward replays
+// the forward's arithmetic exactly). The centre relative to the tile origin is
+// split into a part h on a 2^-12 pixel grid and a remainder l (|l| <= 2^-13 px,
+// carried from the projection's float-float centre): a pixel centre minus h is
+// exact in FP32, and l enters through the linear and constant terms of the
+// expanded exponent, so no offset is rounded at the tile's scale. With
+// X = px - h, Y = py - h_y and the stored conic (A, B', C) (k log2 e folded in):
+//   p2 = A dx^2 + B' dx dy + C dy^2, dx = X - l_x, dy = Y - l_y,
+//      = X (A X + B' Y + a) + Y (C Y + b) + c0,
+//   a = -(2 A l_x + B' l_y), b = -(B' l_x + 2 C l_y), c0 = A l_x^2 + B' l_x l_y + C l_y^2,
+// and alpha = opacity 2^-p2 = 2^(L - (p2 - c0)) with L = log2(opacity) - c0.
+struct StagedSplat {
+  float4 geo;   // h_x, h_y, A, B'
+  float4 geo2;  // C, L, a, b
+  float lx, ly;
+};
+
+__device__ __forceinline__ float2 split_tile_offset(float hi, float lo, float origin) {
+  // hi - origin exactly as s + e (TwoSum), then s = h + (s - h) with h on the grid
+  const float s = __fadd_rn(hi, -origin), bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-origin, bb));
+  const float h = __fmul_rn(rintf(__fmul_rn(s, 4096.f)), 1.f / 4096.f);
+  return make_float2(h, __fadd_rn(__fsub_rn(s, h), __fadd_rn(e, lo)));  // s - h is exact
+}
+
+// smean = (x_hi, y_hi, x_lo, y_lo), sconic = (A, B', C, opacity)
+__device__ __forceinline__ StagedSplat stage_splat(float4 m, float4 k, float x0f, float y0f) {
+  const float2 ox = split_tile_offset(m.x, m.z, x0f), oy = split_tile_offset(m.y, m.w, y0f);
+  const float lx = ox.y, ly = oy.y;
+  const float a = -fmaf(2.f * k.x, lx, k.y * ly), b = -fmaf(k.y, lx, 2.f * k.z * ly);
+  const float c0 = fmaf(k.x * lx, lx, fmaf(k.y * lx, ly, k.z * ly * ly));
+  StagedSplat st;
+  st.geo = make_float4(ox.x, oy.x, k.x, k.y);
+  st.geo2 = make_float4(k.z, log2f(k.w) - c0, a, b);
+  st.lx = lx;
+  st.ly = ly;
+  return st;
+}
+
+// p2 - c0 at the pixel centre (fpx, fpy) relative to the tile origin.
+__device__ __forceinline__ float staged_exponent(const float4 &ge, const float4 &ge2, float fpx,
+                                                 float fpy, float &X, float &Y) {
+  X = fpx - ge.x;
+  Y = fpy - ge.y;
+  return fmaf(X, fmaf(ge.z, X, fmaf(ge.w, Y, ge2.z)), Y * fmaf(ge2.x, Y, ge2.w));
+}
+
 struct RasterArgs {
   const float4 *smean, *sconic;
   const float *grad;
@@ -219,6 +267,7 @@ struct RasterArgs {
   const uint32_t *active;   // [T] active tile ids (when use_active)
   int use_active;           // 1: only active tiles (count in ctrl->n_active)
   int Q, W, H, tiles_x, T;  // Q attribute floats per Gaussian = output planes
+  int grad_pairs;           // set by launch_raster: Q even and grad 8-byte aligned
   float alpha_min, alpha_max, t_min;
   float *maps;              // [Q][H][W]
   Ctrl *ctrl;

@@ -9,11 +9,13 @@
 //   acc += g a T, T -= a T, stop once T < t_min.
 // Tiles no splat reaches are never launched (the field is sparse, Sec. 2.2).
 //
-// The splat centre is staged relative to the tile origin from its (hi, lo) pair,
-// so the per-pixel offset d keeps FP32 relative precision anywhere in the image.
-// exp is evaluated as ex2.approx on -k log2(e) d^T conic d (the factor is folded
-// into the conic at projection); splats whose exponent already puts them below
-// alpha_min (with a 1e-3 margin in the exponent) are skipped without the exp.
+// The splat is staged relative to the tile origin (stage_splat): its centre's
+// (hi, lo) pair becomes a grid part that pixel centres subtract exactly and a
+// remainder folded into the expanded exponent, so alpha keeps FP32 relative
+// precision anywhere in the image. alpha = 2^(L - p2) with L = log2(opacity)
+// (ex2.approx; k log2 e is folded into the conic at projection); splats whose
+// exponent already puts them below alpha_min (with a 1e-3 margin in the
+// exponent) are skipped without the exponential.
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -32,8 +34,8 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   constexpr int QV = (Q + 3) / 4;  // float4 slots of the gradient attribute
   // splat batch, packed so that one pixel-splat evaluation reads 2 broadcast
   // 16-byte words (plus QV more when the splat contributes)
-  __shared__ float4 s_geo[256];   // mx, my (tile-relative), conic a, conic 2b
-  __shared__ float4 s_geo2[256];  // conic c, opacity, exponent limit, -
+  __shared__ float4 s_geo[256];   // h_x, h_y (tile-relative grid part), conic A, B'
+  __shared__ float4 s_geo2[256];  // conic C, L, linear terms a, b (see StagedSplat)
   __shared__ float4 s_g[QV][256];
   const unsigned ntiles = a.use_active ? a.ctrl->n_active : (unsigned)a.T;
   if (blockIdx.x >= ntiles) return;
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   const float x0f = (float)x0, y0f = (float)y0;
   const uint2 rg = a.range[tile];
   const float amin = a.alpha_min, amax = a.alpha_max, tmin = a.t_min;
+  const float cut = log2f(amin) - 1e-3f;  // skip when L - p2 < cut
 
   float acc[QV * 4];
 #pragma unroll
@@ -59,14 +62,24 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
     const unsigned j = s + threadIdx.x;
     if (j < rg.y) {
       const uint32_t g = a.pval[j];
-      const float4 m = a.smean[g];
-      const float4 k = a.sconic[g];
-      s_geo[threadIdx.x] = make_float4((m.x - x0f) + m.z, (m.y - y0f) + m.w, k.x, k.y);
-      s_geo2[threadIdx.x] = make_float4(k.z, k.w, log2f(k.w / amin) + 1e-3f, 0.f);
+      const StagedSplat st = stage_splat(a.smean[g], a.sconic[g], x0f, y0f);
+      s_geo[threadIdx.x] = st.geo;
+      s_geo2[threadIdx.x] = st.geo2;
       const float *gp = a.grad + (size_t)g * Q;
       float gv[QV * 4];
 #pragma unroll
-      for (int q = 0; q < QV * 4; ++q) gv[q] = q < Q ? gp[q] : 0.f;
+      for (int q = 0; q < QV * 4; ++q) gv[q] = 0.f;
+      if (Q % 2 == 0 && a.grad_pairs) {  // 8-byte aligned rows: one 8-byte load per two floats
+#pragma unroll
+        for (int q = 0; q < Q; q += 2) {
+          const float2 v2 = __ldg(reinterpret_cast<const float2 *>(gp + q));
+          gv[q] = v2.x;
+          gv[q + 1] = v2.y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) gv[q] = __ldg(gp + q);
+      }
 #pragma unroll
       for (int v = 0; v < QV; ++v)
         s_g[v][threadIdx.x] = make_float4(gv[4 * v], gv[4 * v + 1], gv[4 * v + 2], gv[4 * v + 3]);
@@ -77,10 +90,10 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
       for (int k = 0; k < cnt; ++k) {
         const float4 ge = s_geo[k];
         const float4 ge2 = s_geo2[k];
-        const float dx = fpx - ge.x, dy = fpy - ge.y;
-        const float p2 = dx * fmaf(ge.z, dx, ge.w * dy) + ge2.x * dy * dy;
-        if (p2 > ge2.z) continue;
-        const float al = fminf(amax, ge2.y * ex2_approx(-p2));
+        float X, Y;
+        const float t = ge2.y - staged_exponent(ge, ge2, fpx, fpy, X, Y);
+        if (t < cut) continue;
+        const float al = fminf(amax, ex2_approx(t));
         if (al < amin) continue;
         const float w = __fmul_rn(al, T);
 #pragma unroll
@@ -109,8 +122,10 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
 
 }  // namespace
 
-cudaError_t launch_raster(const RasterArgs &a, cudaStream_t st) {
-  if (a.T == 0) return cudaSuccess;
+cudaError_t launch_raster(const RasterArgs &a_in, cudaStream_t st) {
+  if (a_in.T == 0) return cudaSuccess;
+  RasterArgs a = a_in;
+  a.grad_pairs = (a.Q % 2 == 0 && (reinterpret_cast<uintptr_t>(a.grad) & 7u) == 0) ? 1 : 0;
   LaunchScope ls_("raster", st);
   switch (a.Q) {
     case 1: launch_k(raster_kernel<1>, a.T, 256, 0, st, a); break;

@@ -29,8 +29,14 @@ def test_algorithmic_bytes_formulas():
     px = C * H * W
     assert bench.algorithmic_bytes("divergence", C, H, W, 5, 0, 0) == px * 12
     assert bench.algorithmic_bytes("finalize", C, H, W, 5, 0, 0) == px * 16
-    assert bench.algorithmic_bytes("mg0_down", C, H, W, 5, 0, 0) == 5 * px * 9
-    assert bench.algorithmic_bytes("mg0_up", C, H, W, 5, 0, 0) == 5 * px * 21 + 4 * px * 8
+    # the survey's per-unknown model: 12 B per sweep, 9 B residual + restriction, 9 B
+    # prolongation + correction; V(2,1) by default
+    assert bench.algorithmic_bytes("mg0_down", C, H, W, 5, 0, 0) == 5 * px * (2 * 12 + 9)
+    assert bench.algorithmic_bytes("mg0_up", C, H, W, 5, 0, 0) == 5 * px * (12 + 9)
+    assert bench.algorithmic_bytes("mg0_up", C, H, W, 5, 0, 0, nu1=3, nu2=2) == 5 * px * (24 + 9)
+    # what the fused kernels must move at least
+    assert bench.min_traffic_bytes("mg0_down", C, H, W, 5, 0, 0) == 5 * px * 9
+    assert bench.min_traffic_bytes("mg0_up", C, H, W, 5, 0, 0) == 5 * px * 21 + 4 * px * 8
     assert bench.algorithmic_bytes("raster", C, H, W, 5, 0, 1000) == 1000 * (36 + 8 * C) + px * 8
     assert bench.algorithmic_bytes("no_such_kernel", C, H, W, 5, 0, 0) == 0.0
 

@@ -30,11 +30,16 @@ def _one(mean, scale, quat, opacity=0.8, grad=None, C=3):
 
 
 def _w2c(cam):
-    return np.asarray(cam.world_to_cam, np.float64)
+    return np.asarray(cam.world_to_cam, np.float32).astype(np.float64)
+
+
+def _f32(v):  # the camera reaches the library as float32 (gdgs_camera)
+    return float(np.float32(v))
 
 
 def _pinhole(cam, x_cam):
-    return np.array([cam.fx * x_cam[0] / x_cam[2] + cam.cx, cam.fy * x_cam[1] / x_cam[2] + cam.cy])
+    return np.array([_f32(cam.fx) * x_cam[0] / x_cam[2] + _f32(cam.cx),
+                     _f32(cam.fy) * x_cam[1] / x_cam[2] + _f32(cam.cy)])
 
 
 # ------------------------------------------------------------------ projection (Eq. sig2d)
