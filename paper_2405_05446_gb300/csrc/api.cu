@@ -95,6 +95,7 @@ bool make_plan(int64_t n, int C, int W, int H, const gdgs_raster_opts &ro,
   // the cached coarse factor sits at a fixed offset with room for the largest
   // coarsest grid, so workspaces laid out for other sizes never overwrite it
   p->off_coarse = cv.take(kCoarseTagBytes + sizeof(double) * (size_t)kMaxCoarse * kMaxCoarse);
+  p->off_sub = cv.take(sizeof(Ctrl) * (size_t)C);
   if (n > 0) {
     p->off_smean = cv.take(16 * (size_t)n);
     p->off_sconic = cv.take(16 * (size_t)n);

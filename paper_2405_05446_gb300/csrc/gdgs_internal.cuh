@@ -45,6 +45,10 @@ struct Ctrl {
   double rho_sq[GDGS_MAX_CHANNELS];
   float rho_mean[GDGS_MAX_CHANNELS];         // the constant removed from rho (least squares)
   float escale[kMaxCycles + 1];              // cycle k solves for s_k e (a power of two)
+  // channel split: every channel ran its own cycle loop (control block of its
+  // own, off_sub); kf_c[c] is the cycle count of channel c's returned iterate
+  int split;
+  int kf_c[GDGS_MAX_CHANNELS];
 };
 
 // Diagnostics hooks around every kernel launch (diag.cu).
@@ -135,6 +139,7 @@ struct Plan {
   size_t off_lu[kMaxLevels], off_lf[kMaxLevels];       // levels >= 1: down-pass u, f
   size_t off_luo[kMaxLevels];                          // levels >= 1: up-pass u (never in place)
   size_t off_coarse;                                   // tag + FP64 inverse
+  size_t off_sub;                                      // per-channel control blocks [C]
   int levels;         // number of levels (finest = 0, coarsest = levels-1)
   int nc;             // unknowns on the coarsest level
   LevelGeom lv[kMaxLevels];

@@ -1158,57 +1158,36 @@ __device__ __forceinline__ float tail_residual(const TailLevel &t, int I, int J,
   return t.f[q] - ((wy * t.cE[J] * dE + wy * t.cW[J] * dW) + (wx * cS * dS + wx * cN * dN));
 }
 
-__global__ void __launch_bounds__(kTailThreads)
-mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
-  griddep_enter();
-  extern __shared__ float4 sm4[];
-  float *S = reinterpret_cast<float *>(sm4);
-  const int k = cycle_index(ctrl, k_in);
-  if (block_should_stop(ctrl, k, first)) return;
-  const int c = blockIdx.x;
+// Stage the coarse inverse into shared memory (transposed) when it is small.
+__device__ void tail_stage_inverse(float *S, const TailArgs &a) {
+  const int tid = threadIdx.x;
+  if (a.off_minv < 0) return;
+  const int nc = (int)a.lv[a.n - 1].plane, n2 = nc * nc;
+  double *M = reinterpret_cast<double *>(S + a.off_minv);
+  for (int q0 = tid; q0 < n2; q0 += 4 * kTailThreads) {
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j * kTailThreads;
+      v[j] = q < n2 ? __ldg(a.Minv + q) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j * kTailThreads;
+      if (q < n2) {
+        const int row = q / nc;
+        M[(q - row * nc) * nc + row] = v[j];
+      }
+    }
+  }
+}
+
+// The tail's part of one V-cycle, in one CTA: from the right-hand side of its
+// first level (already in shared memory, tables built) to the corrected u of
+// that level. Phases are separated by __syncthreads.
+__device__ void tail_vcycle(float *S, const TailArgs &a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int kWarps = kTailThreads / 32;
-
-  {  // right-hand side of the top level and the coarse inverse: loads first
-    const TailLevel t = tail_level_at(S, a, 0);
-    const void *src = s_at(a.f_top, (size_t)c * a.lv[0].plane, a.sf);
-    const int np = (int)a.lv[0].plane;
-    for (int q0 = tid; q0 < np; q0 += 4 * kTailThreads) {
-      float v[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int q = q0 + j * kTailThreads;
-        v[j] = q < np ? s_ld(src, q, a.sf) * a.fin : 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int q = q0 + j * kTailThreads;
-        if (q < np) t.f[q] = v[j];
-      }
-    }
-    if (a.off_minv >= 0) {
-      const int nc = (int)a.lv[a.n - 1].plane, n2 = nc * nc;
-      double *M = reinterpret_cast<double *>(S + a.off_minv);
-      for (int q0 = tid; q0 < n2; q0 += 4 * kTailThreads) {
-        double v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = q0 + j * kTailThreads;
-          v[j] = q < n2 ? __ldg(a.Minv + q) : 0.0;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = q0 + j * kTailThreads;
-          if (q < n2) {
-            const int row = q / nc;
-            M[(q - row * nc) * nc + row] = v[j];
-          }
-        }
-      }
-    }
-    tail_build_tables(S, a);
-    __syncthreads();
-  }
   for (int i = 0; i + 1 < a.n; ++i) {  // down: sweeps from 0, restrict the residual
     const TailLevel t = tail_level_at(S, a, i), tc = tail_level_at(S, a, i + 1);
     for (int s = 0; s < 2 * a.nu1; ++s) {
@@ -1299,6 +1278,39 @@ mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
       __syncthreads();
     }
   }
+}
+
+__global__ void __launch_bounds__(kTailThreads)
+mg_tail_kernel(TailArgs a, Ctrl *ctrl, int k_in, int first) {
+  griddep_enter();
+  extern __shared__ float4 sm4[];
+  float *S = reinterpret_cast<float *>(sm4);
+  const int k = cycle_index(ctrl, k_in);
+  if (block_should_stop(ctrl, k, first)) return;
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x;
+  {  // right-hand side of the top level and the coarse inverse: loads first
+    const TailLevel t = tail_level_at(S, a, 0);
+    const void *src = s_at(a.f_top, (size_t)c * a.lv[0].plane, a.sf);
+    const int np = (int)a.lv[0].plane;
+    for (int q0 = tid; q0 < np; q0 += 4 * kTailThreads) {
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + j * kTailThreads;
+        v[j] = q < np ? s_ld(src, q, a.sf) * a.fin : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + j * kTailThreads;
+        if (q < np) t.f[q] = v[j];
+      }
+    }
+    tail_stage_inverse(S, a);
+    tail_build_tables(S, a);
+    __syncthreads();
+  }
+  tail_vcycle(S, a);
   {
     const TailLevel t = tail_level_at(S, a, 0);
     void *dst = s_at(a.u_top, (size_t)c * a.lv[0].plane, a.sf);
@@ -1348,7 +1360,7 @@ __device__ __forceinline__ float residual_scale(double rnorm2, long long cells) 
 
 __global__ void __launch_bounds__(1024)
 coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl *ctrl, int C,
-                    long long npx) {
+                    long long npx, Ctrl *sub) {
   griddep_enter();
   __shared__ int match;
   __shared__ double fcol[260];
@@ -1362,6 +1374,27 @@ coarse_setup_kernel(LevelGeom g, double *A, CoarseTag *tag, CoarseTag want, Ctrl
     }
     ctrl->rnorm2[0] = r2;
     ctrl->escale[0] = residual_scale(r2, (long long)C * npx);
+    ctrl->split = sub ? 1 : 0;
+  }
+  if (sub) {  // the per-channel control blocks of a channel-split solve
+    int *w = reinterpret_cast<int *>(sub);
+    const int nw = (int)(sizeof(Ctrl) / sizeof(int)) * C;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) w[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < C) {
+      const int c = threadIdx.x;
+      Ctrl *sc = sub + c;
+      const double m = ctrl->rho_sum[c] / (double)npx;
+      const double r2 = fmax(ctrl->rho_sq[c] - ctrl->rho_sum[c] * m, 0.0);
+      sc->rtol = ctrl->rtol;
+      sc->max_cycles = ctrl->max_cycles;
+      sc->channels = 1;
+      sc->rho_mean[0] = (float)m;
+      sc->rho_sum[0] = ctrl->rho_sum[c];
+      sc->rho_sq[0] = ctrl->rho_sq[c];
+      sc->rnorm2[0] = r2;
+      sc->escale[0] = residual_scale(r2, npx);
+    }
   }
   if (threadIdx.x == 0) {
     const CoarseTag t = *tag;
@@ -1571,8 +1604,8 @@ __device__ __forceinline__ float channel_mean(const float (&mean)[GDGS_MAX_CHANN
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   griddep_enter();
   const int stopped = ctrl->stopped;
-  const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
   const int c = blockIdx.y;
+  const int kf = ctrl->split ? ctrl->kf_c[c] : (stopped ? ctrl->cycles : ctrl->max_cycles);
   const LevelGeom &g = a.g0;
   const size_t plane = (size_t)g.H * g.W;
   const float mc = channel_mean(a.mean, c);
@@ -1602,7 +1635,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a, Ctrl *ctrl) {
   if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctrl->mean_set[c] = mc;
-    if (c == 0 && !stopped) ctrl->cycles = kf;
+    if (c == 0 && !stopped && !ctrl->split) ctrl->cycles = kf;
   }
 }
 
@@ -1625,8 +1658,8 @@ __device__ __forceinline__ float fin_px(float h, float l, float eh, float el, fl
 __global__ void __launch_bounds__(256) finalize4_kernel(FinArgs a, Ctrl *ctrl) {
   griddep_enter();
   const int stopped = ctrl->stopped;
-  const int kf = stopped ? ctrl->cycles : ctrl->max_cycles;
   const int c = blockIdx.y;
+  const int kf = ctrl->split ? ctrl->kf_c[c] : (stopped ? ctrl->cycles : ctrl->max_cycles);
   const LevelGeom &g = a.g0;
   const int W = g.W, H = g.H, Wq = W >> 2, nq = H * Wq;
   const size_t plane = (size_t)H * W;
@@ -1667,7 +1700,7 @@ __global__ void __launch_bounds__(256) finalize4_kernel(FinArgs a, Ctrl *ctrl) {
   if (threadIdx.x == 0) atomicAdd(&ctrl->final_rnorm2, (double)r2);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctrl->mean_set[c] = mc;
-    if (c == 0 && !stopped) ctrl->cycles = kf;
+    if (c == 0 && !stopped && !ctrl->split) ctrl->cycles = kf;
   }
 }
 
@@ -1698,6 +1731,26 @@ __global__ void advance_kernel(Ctrl *ctrl, int k_in, cudaGraphConditionalHandle 
     atomicAdd(&g_graph_kernels, (unsigned long long)kernels_per_cycle);
     cudaGraphSetConditional(h, (!ctrl->stopped && k + 1 < ctrl->max_cycles) ? 1u : 0u);
   }
+}
+
+// After channel-split cycle loops: the all-channel state the finalize kernel and
+// gdgs_sync_status read. A channel's iterate is the one its own loop stopped at
+// (or its last, if it did not converge).
+__global__ void merge_channels_kernel(Ctrl *ctrl, const Ctrl *sub, int C) {
+  griddep_enter();
+  if (threadIdx.x != 0) return;
+  int all = 1, kmax = 0;
+  for (int c = 0; c < C; ++c) {
+    const Ctrl &s = sub[c];
+    const int kc = s.stopped ? s.cycles : s.max_cycles;
+    ctrl->kf_c[c] = kc;
+    ctrl->sum_u[kc][c] = s.sum_u[kc][0];
+    all &= s.stopped;
+    kmax = max(kmax, kc);
+    if (s.status != GDGS_OK) set_status(ctrl, s.status);
+  }
+  ctrl->stopped = all;
+  ctrl->cycles = kmax;
 }
 
 // ------------------------------------------------------------------ host side
@@ -1793,24 +1846,32 @@ struct Cycle {
   int storage;
   const double *Minv;
 
+  int chan = 0;  // channel-split loop: the one channel it solves (C == 1, pointers offset)
+
+  // level-l array at byte offset off (storage format), FP32 finest-level array
+  char *lvl(size_t off, int l) const {
+    return ws + off + (size_t)chan * (size_t)p->lv[l].plane * (storage == GDGS_STORAGE_F32 ? 4 : 2);
+  }
+  char *fin0(size_t off) const { return ws + off + (size_t)chan * (size_t)p->lv[0].plane * 4; }
+
   LvArgs level(int l) const {
     LvArgs a{};
     a.g = p->lv[l];
     a.gc = p->lv[l + 1];
-    a.f = l > 0 ? (const void *)(ws + p->off_lf[l]) : nullptr;
-    a.u = ws + (l > 0 ? p->off_lu[l] : p->off_e0);
-    a.uo = l > 0 ? (void *)(ws + p->off_luo[l]) : nullptr;
-    a.fc = ws + p->off_lf[l + 1];
-    a.uc = ws + p->off_luo[l + 1];
+    a.f = l > 0 ? (const void *)lvl(p->off_lf[l], l) : nullptr;
+    a.u = l > 0 ? lvl(p->off_lu[l], l) : lvl(p->off_e0, 0);
+    a.uo = l > 0 ? (void *)lvl(p->off_luo[l], l) : nullptr;
+    a.fc = lvl(p->off_lf[l + 1], l + 1);
+    a.uc = lvl(p->off_luo[l + 1], l + 1);
     a.sf = storage;
     a.fin = ldexpf(1.f, 2 * l);
     a.fout = ldexpf(1.f, -2 * (l + 1));
     a.level0 = l == 0;
-    a.rho = (const float *)(ws + p->off_rho);
-    a.rb[0] = (float *)(ws + p->off_r[0]);
-    a.rb[1] = (float *)(ws + p->off_r[1]);
-    a.uhi = (float *)(ws + p->off_uhi);
-    a.ulo = (float *)(ws + p->off_ulo);
+    a.rho = (const float *)fin0(p->off_rho);
+    a.rb[0] = (float *)fin0(p->off_r[0]);
+    a.rb[1] = (float *)fin0(p->off_r[1]);
+    a.uhi = (float *)fin0(p->off_uhi);
+    a.ulo = (float *)fin0(p->off_ulo);
     a.omega = omega;
     return a;
   }
@@ -1823,8 +1884,8 @@ struct Cycle {
     a.n = p->levels - t;
     for (int i = 0; i < a.n; ++i) a.lv[i] = p->lv[t + i];
     tail_layout(a.lv, a.n, &a);
-    a.f_top = ws + p->off_lf[t];
-    a.u_top = ws + p->off_luo[t];
+    a.f_top = lvl(p->off_lf[t], t);
+    a.u_top = lvl(p->off_luo[t], t);
     a.sf = storage;
     a.fin = ldexpf(1.f, 2 * t);
     a.Minv = Minv;
@@ -1899,14 +1960,16 @@ struct Cycle {
 struct GraphKey {
   int dev;
   const void *ws;
+  const void *ctrl;  // the loop's control block (one per channel in a split solve)
+  int chan;
   int C, H, W, nu1, nu2, max_cycles, levels, storage;
   float omega;
   size_t off_rho, off_coarse, total;
   bool operator<(const GraphKey &o) const {
-    return std::tie(dev, ws, C, H, W, nu1, nu2, max_cycles, levels, storage, omega, off_rho,
-                    off_coarse, total) <
-           std::tie(o.dev, o.ws, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles, o.levels, o.storage,
-                    o.omega, o.off_rho, o.off_coarse, o.total);
+    return std::tie(dev, ws, ctrl, chan, C, H, W, nu1, nu2, max_cycles, levels, storage, omega,
+                    off_rho, off_coarse, total) <
+           std::tie(o.dev, o.ws, o.ctrl, o.chan, o.C, o.H, o.W, o.nu1, o.nu2, o.max_cycles,
+                    o.levels, o.storage, o.omega, o.off_rho, o.off_coarse, o.total);
   }
 };
 
@@ -2044,6 +2107,64 @@ inline bool quad_path(int W, const void *p0, const void *p1) {
   return W % 4 == 0 && ((uintptr_t)p0 % 16) == 0 && ((uintptr_t)p1 % 16) == 0;
 }
 
+bool split_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("GDGS_SPLIT");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+// Helper streams and events of channel-split solves, one set per (device,
+// caller stream), so that calls on different caller streams never share a
+// helper stream; at most kMaxForkSets sets, the least recently used replaced.
+struct ForkSet {
+  cudaStream_t s[GDGS_MAX_CHANNELS] = {};
+  cudaEvent_t ev[GDGS_MAX_CHANNELS] = {};
+  unsigned long long last_use = 0;
+};
+constexpr size_t kMaxForkSets = 32;
+
+cudaError_t fork_set(cudaStream_t st, ForkSet **out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, cudaStream_t>, ForkSet> sets;
+  static unsigned long long clock = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(dev, st);
+  auto it = sets.find(key);
+  if (it == sets.end()) {
+    if (sets.size() >= kMaxForkSets) {
+      auto lru = sets.begin();
+      for (auto jt = sets.begin(); jt != sets.end(); ++jt)
+        if (jt->second.last_use < lru->second.last_use) lru = jt;
+      for (int c = 0; c < GDGS_MAX_CHANNELS; ++c) {
+        if (lru->second.s[c]) cudaStreamDestroy(lru->second.s[c]);
+        if (lru->second.ev[c]) cudaEventDestroy(lru->second.ev[c]);
+      }
+      sets.erase(lru);
+    }
+    ForkSet f;
+    for (int c = 0; c < GDGS_MAX_CHANNELS && e == cudaSuccess; ++c) {
+      if (c > 0) e = cudaStreamCreateWithFlags(&f.s[c], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev[c], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      for (int c = 0; c < GDGS_MAX_CHANNELS; ++c) {
+        if (f.s[c]) cudaStreamDestroy(f.s[c]);
+        if (f.ev[c]) cudaEventDestroy(f.ev[c]);
+      }
+      return e;
+    }
+    it = sets.emplace(key, f).first;
+  }
+  it->second.last_use = ++clock;
+  *out = &it->second;
+  return cudaSuccess;
+}
+
 cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   const Plan &p = *a.plan;
   char *ws = a.ws;
@@ -2083,10 +2204,12 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   want.version = 1;
   CoarseTag *tag = (CoarseTag *)(ws + p.off_coarse);
   double *Minv = (double *)(ws + p.off_coarse + kCoarseTagBytes);
+  const bool split = a.C > 1 && split_enabled();
+  Ctrl *sub = split ? (Ctrl *)(ws + p.off_sub) : nullptr;
   {
     LaunchScope ls_("coarse_setup", st);
     launch_k(coarse_setup_kernel, 1, 1024, 0, st, gcoarse, Minv, tag, want, ctrl, a.C,
-                                            (long long)a.H * a.W);
+                                            (long long)a.H * a.W, sub);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -2100,24 +2223,67 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   cy.omega = a.omega;
   cy.storage = a.storage;
   cy.Minv = Minv;
-
   if ((e = cy.prepare()) != cudaSuccess) return e;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
-  if (cap == cudaStreamCaptureStatusActive && graphs_enabled() && !diag_profiling()) {
-    if ((e = capture_cycle_loop(cy, st)) != cudaSuccess) return e;
-  } else if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const GraphKey key{dev,       ws,      a.C,       a.H,          a.W,    a.nu1, a.nu2,
-                       a.max_cycles, p.levels, a.storage, a.omega, p.off_rho, p.off_coarse,
-                       p.total};
-    if ((e = launch_cycle_graph(cy, key, st)) != cudaSuccess) return e;
-  } else {
+
+  // The cycle loop of one Cycle on stream s: a WHILE node recorded into the
+  // caller's capture, a cached graph, or direct launches.
+  auto run_loop = [&](const Cycle &c, cudaStream_t s) -> cudaError_t {
+    if (cap == cudaStreamCaptureStatusActive && graphs_enabled() && !diag_profiling())
+      return capture_cycle_loop(c, s);
+    if (graphs_enabled() && !diag_profiling() && cap == cudaStreamCaptureStatusNone) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      const GraphKey key{dev,          ws,       c.ctrl,   c.chan,  c.C,       a.H,
+                         a.W,          a.nu1,    a.nu2,    a.max_cycles, p.levels, a.storage,
+                         a.omega,      p.off_rho, p.off_coarse, p.total};
+      return launch_cycle_graph(c, key, s);
+    }
     // direct launches: every cycle is enqueued; once the advance kernel has
     // recorded convergence the remaining ones return at their first check
-    for (int k = 0; k < a.max_cycles; ++k)
-      if ((e = cy.launch(k, 0, 0, st)) != cudaSuccess) return e;
+    for (int k = 0; k < a.max_cycles; ++k) {
+      const cudaError_t e2 = c.launch(k, 0, 0, s);
+      if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+  };
+
+  if (!split) {
+    if ((e = run_loop(cy, st)) != cudaSuccess) return e;
+  } else {
+    // Channel split: each channel's cycle loop on a stream of its own (channel 0
+    // on the caller's stream), so the latency-bound small levels of one channel
+    // overlap the bandwidth-bound large levels of the others. A channel stops
+    // when its own relative residual reaches rtol, which implies the
+    // all-channel criterion. Forked from and joined back to the caller's stream
+    // by events, so the call keeps plain stream order (and is capturable).
+    // While the per-kernel profiler records, the channels' loops run one after
+    // another on the caller's stream, so that each launch is timed alone.
+    const bool fork = !diag_profiling();
+    ForkSet *fk = nullptr;
+    if (fork) {
+      if ((e = fork_set(st, &fk)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(fk->ev[0], st)) != cudaSuccess) return e;
+      for (int c = 1; c < a.C; ++c)
+        if ((e = cudaStreamWaitEvent(fk->s[c], fk->ev[0], 0)) != cudaSuccess) return e;
+    }
+    for (int c = 0; c < a.C; ++c) {
+      Cycle cc = cy;
+      cc.C = 1;
+      cc.chan = c;
+      cc.ctrl = sub + c;
+      if ((e = run_loop(cc, (c == 0 || !fork) ? st : fk->s[c])) != cudaSuccess) return e;
+    }
+    for (int c = 1; fork && c < a.C; ++c) {
+      if ((e = cudaEventRecord(fk->ev[c], fk->s[c])) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(st, fk->ev[c], 0)) != cudaSuccess) return e;
+    }
+    {
+      LaunchScope ls_("merge_channels", st);
+      launch_k(merge_channels_kernel, 1, 32, 0, st, ctrl, (const Ctrl *)sub, a.C);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
   FinArgs fa{};
