@@ -16,6 +16,12 @@
 // (ex2.approx; k log2 e is folded into the conic at projection); splats whose
 // exponent already puts them below alpha_min (with a 1e-3 margin in the
 // exponent) are skipped without the exponential.
+//
+// A warp holds two pixel rows of the tile. When a batch is staged, every splat
+// also gets the mask of the warps whose rows its ellipse can reach (closed form,
+// with the binning's margins), and each warp compacts the batch into a list of
+// its own in front-to-back order, so a warp never evaluates a splat that cannot
+// reach its rows (they would all have been skipped by the exponent test).
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -28,6 +34,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Warps whose two pixel rows the splat's ellipse p2 <= log2(opacity / alpha_min)
+// + 1e-3 (the exponent cut of the composite) can reach, widened like the
+// binning's cut (0.1 % + 0.01) so that no reachable row is dropped. The
+// ellipse's vertical half-extent is sqrt(lim 4A / (4AC - B'^2)) around the
+// centre h_y + l_y (tile-relative rows; pixel row r has its centre at r + 0.5).
+__device__ __forceinline__ uint8_t warp_rows_mask(const StagedSplat &st, float4 k, float amin) {
+  const float A = k.x, B = k.y, C = k.z;
+  const float lim = (log2f(k.w / amin) + 1e-3f) * 1.001f + 0.01f;
+  const float D = fmaf(4.f * A, C, -B * B);
+  if (!(lim > 0.f) || !(D > 0.f)) return 0xffu;  // degenerate: keep for every warp
+  const float hy = sqrtf(lim * 4.f * A / D) * 1.0001f + 1e-3f;
+  const float cy = st.geo.y + st.ly;
+  const float r0 = ceilf(cy - hy - 0.5f), r1 = floorf(cy + hy - 0.5f);  // reachable pixel rows
+  if (!(r1 >= 0.f) || !(r0 <= (float)(kTile - 1))) return 0u;
+  const int i0 = max(0, (int)r0) >> 1, i1 = min(kTile - 1, (int)r1) >> 1;
+  return (uint8_t)(((2u << i1) - 1u) & ~((1u << i0) - 1u));
+}
+
 template <int Q>
 __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   griddep_enter();
@@ -37,6 +61,9 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   __shared__ float4 s_geo[256];   // h_x, h_y (tile-relative grid part), conic A, B'
   __shared__ float4 s_geo2[256];  // conic C, L, linear terms a, b (see StagedSplat)
   __shared__ float4 s_g[QV][256];
+  __shared__ uint8_t s_wmask[256];         // warps (row pairs) each splat of the batch can reach
+  __shared__ uint8_t s_list[8][256];       // per warp: the batch's splats that can reach it
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ntiles = a.use_active ? a.ctrl->n_active : (unsigned)a.T;
   if (blockIdx.x >= ntiles) return;
   const int tile = a.use_active ? (int)a.active[blockIdx.x] : (int)blockIdx.x;
@@ -62,9 +89,11 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
     const unsigned j = s + threadIdx.x;
     if (j < rg.y) {
       const uint32_t g = a.pval[j];
-      const StagedSplat st = stage_splat(a.smean[g], a.sconic[g], x0f, y0f);
+      const float4 kc = a.sconic[g];
+      const StagedSplat st = stage_splat(a.smean[g], kc, x0f, y0f);
       s_geo[threadIdx.x] = st.geo;
       s_geo2[threadIdx.x] = st.geo2;
+      s_wmask[threadIdx.x] = warp_rows_mask(st, kc, amin);
       const float *gp = a.grad + (size_t)g * Q;
       float gv[QV * 4];
 #pragma unroll
@@ -86,8 +115,18 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
     }
     __syncthreads();
     const int cnt = min(256u, rg.y - s);
+    int nl = 0;  // this warp's list, in batch order
+    for (int k0 = 0; k0 < cnt; k0 += 32) {
+      const int k = k0 + lane;
+      const bool in = k < cnt && ((s_wmask[k] >> warp) & 1u);
+      const unsigned b = __ballot_sync(0xffffffffu, in);
+      if (in) s_list[warp][nl + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
+      nl += __popc(b);
+    }
+    __syncwarp();
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
+      for (int i = 0; i < nl; ++i) {
+        const int k = s_list[warp][i];
         const float4 ge = s_geo[k];
         const float4 ge2 = s_geo2[k];
         float X, Y;
