@@ -1778,6 +1778,10 @@ cudaError_t set_smem(size_t bytes) {
   return e;
 }
 
+// Launch names per level (the diagnostics keep the pointer).
+const char *const kDownName[kMaxLevels] = {"mg0_down", "mg1_down", "mg2_down", "mg3_down", "mg4_down", "mg5_down", "mg6_down", "mg7_down", "mg8_down", "mg9_down", "mg10_down", "mg11_down", "mg12_down", "mg13_down", "mg14_down", "mg15_down", "mg16_down", "mg17_down", "mg18_down", "mg19_down", "mg20_down", "mg21_down", "mg22_down", "mg23_down"};
+const char *const kUpName[kMaxLevels] = {"mg0_up", "mg1_up", "mg2_up", "mg3_up", "mg4_up", "mg5_up", "mg6_up", "mg7_up", "mg8_up", "mg9_up", "mg10_up", "mg11_up", "mg12_up", "mg13_up", "mg14_up", "mg15_up", "mg16_up", "mg17_up", "mg18_up", "mg19_up", "mg20_up", "mg21_up", "mg22_up", "mg23_up"};
+
 template <int NU, int TY_, int TX_>
 cudaError_t launch_mg_down_t(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
   using G = Geo<NU, TY_, TX_>;
@@ -1786,7 +1790,7 @@ cudaError_t launch_mg_down_t(const LvArgs &a, Ctrl *ctrl, int k, int first, int 
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
   {
-    LaunchScope ls_(a.level0 ? "mg0_down" : "mg_down", st);
+    LaunchScope ls_(kDownName[a.g.shift], st);
     launch_k(mg_down_kernel<NU, TY_, TX_>, grid, dim3(kBX, kBY), sm, st, a, ctrl, k, first);
   }
   return cudaGetLastError();
@@ -1800,7 +1804,7 @@ cudaError_t launch_mg_up_t(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream
   if (e != cudaSuccess) return e;
   const dim3 grid((a.g.W + TX_ - 1) / TX_, (a.g.H + TY_ - 1) / TY_, C);
   {
-    LaunchScope ls_(a.level0 ? "mg0_up" : "mg_up", st);
+    LaunchScope ls_(kUpName[a.g.shift], st);
     launch_k(mg_up_kernel<NU, TY_, TX_>, grid, dim3(kBX, kBY), sm, st, a, ctrl, k);
   }
   return cudaGetLastError();

@@ -34,6 +34,9 @@ def test_algorithmic_bytes_formulas():
     assert bench.algorithmic_bytes("mg0_down", C, H, W, 5, 0, 0) == 5 * px * (2 * 12 + 9)
     assert bench.algorithmic_bytes("mg0_up", C, H, W, 5, 0, 0) == 5 * px * (12 + 9)
     assert bench.algorithmic_bytes("mg0_up", C, H, W, 5, 0, 0, nu1=3, nu2=2) == 5 * px * (24 + 9)
+    lv, _ = bench.mg_levels(H, W)
+    assert bench.algorithmic_bytes("mg1_down", C, H, W, 5, 0, 0) == 5 * C * lv[1][0] * lv[1][1] * 33
+    assert bench.algorithmic_bytes("mg2_up", C, H, W, 5, 0, 0) == 5 * C * lv[2][0] * lv[2][1] * 21
     # what the fused kernels must move at least
     assert bench.min_traffic_bytes("mg0_down", C, H, W, 5, 0, 0) == 5 * px * 9
     assert bench.min_traffic_bytes("mg0_up", C, H, W, 5, 0, 0) == 5 * px * 21 + 4 * px * 8
