@@ -968,6 +968,627 @@ struct UpShape {
       (2 * G::ARR + (G::CRY * G::CRX + 3) / 4 * 4) * sizeof(float) + sizeof(Factors<G>);
 };
 
+// ------------------------------------------------------------------ finest level: streaming warps
+//
+// The finest level has unit cells: every face coefficient is 1 inside the grid
+// and 0 on its border. With W even and V(2, 1) its down and up passes run as
+// register pipelines instead of tiles. A warp owns a strip of kStripW = 64
+// columns (lane l holds the cell pair sx + 2l, sx + 2l + 1, one cell of each
+// colour in every row) and streams down a segment of rows. Each step loads one
+// row and moves every stage of the pass on by one row, every stage a row behind
+// the one before it, so a stage finds the rows around its own in the state it
+// needs: red-black ordering makes the wavefront give exactly the sweep-by-sweep
+// result. Horizontal neighbours come by warp shuffle; there is no shared memory
+// and no barrier. The outer lanes' shuffles and the rows above the first loaded
+// one give wrong values, which move inward by one cell per stage, so a strip
+// stores its middle 56 columns (strips overlap by 8) and a segment begins as
+// many rows above its first output row as the pass has stages after the first.
+// Steps whose rows, in strips whose columns, are all away from the grid border
+// use the constant coefficients (the tiled kernels' fast formulas); the others
+// take the tiled kernels' general cell formulas.
+
+constexpr int kStripW = 64;          // columns per strip, two per lane
+constexpr int kStripX = 4;           // halo columns on each side of a strip's output
+constexpr int kStripOut = kStripW - 2 * kStripX;
+constexpr int kStreamThreads = 128;  // four independent warps per CTA
+constexpr int kStreamPre = 4;        // rows loaded ahead of their use, per stream (up pass)
+constexpr int kStreamPreDown = 8;    // the same for the down pass's one input stream
+
+struct StreamGrid {
+  int nstrips, nseg, S;  // strips of kStripOut output columns, segments of S output rows (S % 8 == 0)
+};
+
+template <int SF>
+__device__ __forceinline__ float2 s_ld2(const void *p, size_t i) {  // i even
+  if (SF == GDGS_STORAGE_F32) return __ldg(reinterpret_cast<const float2 *>(reinterpret_cast<const float *>(p) + i));
+  const unsigned r = __ldg(reinterpret_cast<const unsigned *>(reinterpret_cast<const unsigned short *>(p) + i));
+  if (SF == GDGS_STORAGE_BF16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r));
+  return __half22float2(*reinterpret_cast<const __half2 *>(&r));
+}
+
+template <int SF>
+__device__ __forceinline__ void s_st2(void *p, size_t i, float2 v) {  // i even
+  if (SF == GDGS_STORAGE_F32) {
+    *reinterpret_cast<float2 *>(reinterpret_cast<float *>(p) + i) = v;
+  } else if (SF == GDGS_STORAGE_BF16) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+    *reinterpret_cast<unsigned *>(reinterpret_cast<unsigned short *>(p) + i) = *reinterpret_cast<const unsigned *>(&b);
+  } else {
+    const __half2 b = __floats2half2_rn(v.x, v.y);
+    *reinterpret_cast<unsigned *>(reinterpret_cast<unsigned short *>(p) + i) = *reinterpret_cast<const unsigned *>(&b);
+  }
+}
+
+template <int I>
+__device__ __forceinline__ float &cell(float2 &v) {
+  if constexpr (I == 0) return v.x;
+  else return v.y;
+}
+
+// West and east neighbours of cell I of a lane's pair in row v: one is the
+// lane's other cell, the other that of the adjacent lane (the outer lanes get
+// their own value back: wrong, and inside the strip's halo).
+template <int I>
+__device__ __forceinline__ void horiz(const float2 &v, float &w, float &e) {
+  if constexpr (I == 0) {
+    w = __shfl_up_sync(0xffffffffu, v.y, 1);
+    e = v.y;
+  } else {
+    w = v.x;
+    e = __shfl_down_sync(0xffffffffu, v.x, 1);
+  }
+}
+
+// Cell formulas. Each is written with explicit roundings (no a * b + c for the
+// compiler to fuse or not), so it is one sequence of operations wherever it is
+// inlined, and which formula a cell gets depends on the cell's position alone,
+// never on the step, strip or segment computing it. So a cell computed by two
+// strips or segments gets the same bits in both, and the update of u and the
+// residuals of the cells next to it use one value of e.
+//
+// A full cell (all four neighbours in the grid) takes the tiled kernels'
+// interior formula; the others a masked form of the same operator, with 0/1
+// face coefficients and 1 / (number of neighbours) from a table.
+
+// Finest-level cell with all four neighbours inside the grid.
+__device__ __forceinline__ bool full_row(const LevelGeom &g, int y) { return y >= 1 && y <= g.H - 2; }
+__device__ __forceinline__ bool full_col(const LevelGeom &g, int x) { return x >= 1 && x <= g.W - 2; }
+
+// 1 / d for d in-grid neighbours (d = 0: a cell outside the grid, which stays 0).
+__device__ __forceinline__ float inv_count(float d) {
+  return d > 3.5f ? 0.25f : d > 2.5f ? (1.f / 3.f) : d > 1.5f ? 0.5f : d > 0.5f ? 1.f : 0.f;
+}
+
+__device__ __forceinline__ float gs_fast(float old, float w, float e, float n, float s, float f,
+                                         float omega) {
+  const float v = __fmul_rn(0.25f, __fsub_rn(__fadd_rn(__fadd_rn(w, e), __fadd_rn(n, s)), f));
+  return omega != 1.f ? fmaf(omega, __fsub_rn(v, old), old) : v;
+}
+
+__device__ __forceinline__ float gs_mask(float old, float w, float e, float n, float s, float f,
+                                         float cw, float ce, float cn, float cs, float invd,
+                                         float omega) {
+  float a = __fmul_rn(ce, e);
+  a = fmaf(cw, w, a);
+  a = fmaf(cs, s, a);
+  a = fmaf(cn, n, a);
+  const float v = __fmul_rn(__fsub_rn(a, f), invd);
+  return fmaf(omega, __fsub_rn(v, old), old);
+}
+
+__device__ __forceinline__ float res_fast(float u, float e, float w, float s, float n, float f) {
+  return __fsub_rn(f, __fadd_rn(__fadd_rn(__fsub_rn(e, u), __fsub_rn(w, u)),
+                                __fadd_rn(__fsub_rn(s, u), __fsub_rn(n, u))));
+}
+
+__device__ __forceinline__ float res_mask(float u, float e, float w, float s, float n, float f,
+                                          float cw, float ce, float cn, float cs) {
+  float a = __fmul_rn(ce, __fsub_rn(e, u));
+  a = fmaf(cw, __fsub_rn(w, u), a);
+  a = fmaf(cs, __fsub_rn(s, u), a);
+  a = fmaf(cn, __fsub_rn(n, u), a);
+  return __fsub_rn(f, a);
+}
+
+// First half-sweep from e = 0: omega (-f / d).
+__device__ __forceinline__ float gs0_fast(float f, float omega) {
+  const float v = __fmul_rn(0.25f, -f);
+  return omega != 1.f ? __fmul_rn(omega, v) : v;
+}
+__device__ __forceinline__ float gs0_mask(float f, float invd, float omega) {
+  const float v = __fmul_rn(-f, invd);
+  return omega != 1.f ? __fmul_rn(omega, v) : v;
+}
+
+// Regular prolongation weights: 3/4 on the nearer value, 1/4 on the farther.
+__device__ __forceinline__ float lerp_reg(float near_, float far_) {
+  return fmaf(0.75f, near_, __fmul_rn(0.25f, far_));
+}
+
+// Row masks of a row for the general steps.
+struct RowMask {
+  float in, cn, cs;  // row inside the grid; north / south neighbour inside
+  bool full;
+};
+
+__device__ __forceinline__ RowMask row_mask(const LevelGeom &g, int y) {
+  RowMask r;
+  const bool in = y >= 0 && y < g.H;
+  r.in = in ? 1.f : 0.f;
+  r.cn = (in && y > 0) ? 1.f : 0.f;
+  r.cs = (in && y < g.H - 1) ? 1.f : 0.f;
+  r.full = full_row(g, y);
+  return r;
+}
+
+// Per-warp strip and segment, the lane's pair and its column masks. Step
+// modes: 0 = rows and columns all full, 1 = rows full (column masks per lane),
+// 2 = general (row masks per row as well).
+struct StripLane {
+  int x;           // column of the lane's even cell
+  bool in;         // the pair lies inside the grid (W even: both cells or neither)
+  bool out;        // the lane stores its pair: a middle lane, inside the grid
+  int y0, y1;      // output rows [y0, y1): y0 a multiple of 8, y1 <= H rounded up to even
+  int sx;          // first column of the strip
+  float inx;       // in, as 0 / 1
+  float cw[2], ce[2];  // west / east neighbour inside, per cell
+  float invd[2];   // 1 / d of each cell in a full row
+  bool fcol[2];    // the cell's column is full
+
+  // Smoother update of cell I of a row (row masks m used in mode 2 only).
+  template <int MODE, int I>
+  __device__ __forceinline__ float sweep(const RowMask &m, float old, float w, float e, float n,
+                                         float s, float f, float omega) const {
+    const float fast = gs_fast(old, w, e, n, s, f, omega);
+    if constexpr (MODE == 0) {
+      return fast;
+    } else if constexpr (MODE == 1) {
+      return fcol[I] ? fast : gs_mask(old, w, e, n, s, f, cw[I], ce[I], inx, inx, invd[I], omega);
+    } else {
+      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
+      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
+      const float id = inv_count(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
+      return (m.full && fcol[I]) ? fast : gs_mask(old, w, e, n, s, f, cwm, cem, cnm, csm, id, omega);
+    }
+  }
+
+  template <int MODE, int I>
+  __device__ __forceinline__ float sweep0(const RowMask &m, float f, float omega) const {
+    const float fast = gs0_fast(f, omega);
+    if constexpr (MODE == 0) {
+      return fast;
+    } else if constexpr (MODE == 1) {
+      return fcol[I] ? fast : gs0_mask(f, invd[I], omega);
+    } else {
+      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
+      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
+      const float id = inv_count(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
+      return (m.full && fcol[I]) ? fast : gs0_mask(f, id, omega);
+    }
+  }
+
+  // Residual of cell I (0 outside the grid: all masks 0 and f = 0 there).
+  template <int MODE, int I>
+  __device__ __forceinline__ float res(const RowMask &m, float u, float e, float w, float s, float n,
+                                       float f) const {
+    const float fast = res_fast(u, e, w, s, n, f);
+    if constexpr (MODE == 0) {
+      return fast;
+    } else if constexpr (MODE == 1) {
+      return fcol[I] ? fast : res_mask(u, e, w, s, n, f, cw[I], ce[I], inx, inx);
+    } else {
+      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
+      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
+      return (m.full && fcol[I]) ? fast : res_mask(u, e, w, s, n, f, cwm, cem, cnm, csm);
+    }
+  }
+};
+
+__device__ __forceinline__ bool strip_lane(const LevelGeom &g, const StreamGrid &sg, StripLane &sl) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * (kStreamThreads / 32) + (threadIdx.x >> 5);
+  if (wid >= sg.nstrips * sg.nseg) return false;
+  const int seg = wid / sg.nstrips, strip = wid - seg * sg.nstrips;
+  sl.sx = strip * kStripOut - kStripX;
+  sl.x = sl.sx + 2 * lane;
+  sl.in = sl.x >= 0 && sl.x < g.W;
+  sl.out = sl.in && lane >= kStripX / 2 && lane < 32 - kStripX / 2;
+  sl.y0 = seg * sg.S;
+  sl.y1 = min(sl.y0 + sg.S, (g.H + 1) & ~1);
+  sl.inx = sl.in ? 1.f : 0.f;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int x = sl.x + i;
+    sl.cw[i] = (sl.in && x > 0) ? 1.f : 0.f;
+    sl.ce[i] = (sl.in && x < g.W - 1) ? 1.f : 0.f;
+    sl.invd[i] = inv_count(__fadd_rn(__fadd_rn(sl.cw[i], sl.ce[i]), __fadd_rn(sl.inx, sl.inx)));
+    sl.fcol[i] = full_col(g, x);
+  }
+  return true;
+}
+
+// Down pass on the finest level (nu1 = 2): stage 0 is the first half-sweep from
+// e = 0 on row t; stages 1-3 the next half-sweeps on rows t-1 .. t-3; row t-3 is
+// then final and stored; the residual of row t-4 is summed into the coarse
+// right-hand side. E[j] and F[j] hold row t - j of e and of the right-hand side.
+template <int SF>
+struct DownStream {
+  LevelGeom g, gc;
+  StripLane sl;
+  const float *src;
+  float off, scale, omega, fout;
+  void *u, *fc;
+  float2 E[6], F[5], Q[kStreamPreDown];
+  float rpair;
+
+  __device__ __forceinline__ float2 load(int row) const {
+    return (sl.in && row >= 0 && row < g.H)
+               ? __ldg(reinterpret_cast<const float2 *>(src + (size_t)row * g.W + sl.x))
+               : make_float2(0.f, 0.f);
+  }
+
+  template <int MODE, int PAR>
+  __device__ __forceinline__ void step(int t) {
+    constexpr int I = PAR;  // every stage of this step updates cell PAR of its row
+#pragma unroll
+    for (int j = 5; j > 0; --j) E[j] = E[j - 1];
+#pragma unroll
+    for (int j = 4; j > 0; --j) F[j] = F[j - 1];
+    const float2 q = Q[0];
+#pragma unroll
+    for (int j = 0; j + 1 < kStreamPreDown; ++j) Q[j] = Q[j + 1];
+    Q[kStreamPreDown - 1] = load(t + kStreamPreDown);
+    const bool rin = MODE == 0 || (sl.in && t >= 0 && t < g.H);
+    F[0] = rin ? make_float2(__fmul_rn(__fsub_rn(q.x, off), scale), __fmul_rn(__fsub_rn(q.y, off), scale))
+               : make_float2(0.f, 0.f);
+    E[0] = make_float2(0.f, 0.f);
+    RowMask m[5];
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int s = 0; s < 5; ++s) m[s] = row_mask(g, t - s);
+    }
+    // stage 0: colour 0 of row t from zero
+    cell<I>(E[0]) = sl.sweep0<MODE, I>(m[0], cell<I>(F[0]), omega);
+    // stages 1-3: colours 1, 0, 1 of rows t-1, t-2, t-3
+#pragma unroll
+    for (int s = 1; s <= 3; ++s) {
+      float w, e;
+      horiz<I>(E[s], w, e);
+      cell<I>(E[s]) = sl.sweep<MODE, I>(m[s], cell<I>(E[s]), w, e, cell<I>(E[s + 1]),
+                                        cell<I>(E[s - 1]), cell<I>(F[s]), omega);
+    }
+    {
+      const int y = t - 3;
+      if (sl.out && y >= sl.y0 && y < sl.y1 && y < g.H) s_st2<SF>(u, (size_t)y * g.W + sl.x, E[3]);
+    }
+    // residual of row t-4, summed over 2 x 2 children into the coarse right-hand side
+    const int y = t - 4;
+    const float2 uu = E[4], n = E[5], so = E[3], f = F[4];
+    const float wl = __shfl_up_sync(0xffffffffu, uu.y, 1);
+    const float er = __shfl_down_sync(0xffffffffu, uu.x, 1);
+    const float r0 = sl.res<MODE, 0>(m[4], uu.x, uu.y, wl, so.x, n.x, f.x);
+    const float r1 = sl.res<MODE, 1>(m[4], uu.y, er, uu.x, so.y, n.y, f.y);
+    const float rs = __fadd_rn(r0, r1);
+    if constexpr (PAR == 0) {
+      rpair = rs;  // row t-4 even: the first row of a coarse row
+    } else {
+      const int ci = (y - 1) >> 1;
+      if (sl.out && y - 1 >= sl.y0 && y - 1 < sl.y1 && ci < gc.H)
+        s_st(fc, (size_t)ci * gc.W + (sl.x >> 1), __fmul_rn(__fadd_rn(rpair, rs), fout), SF);
+    }
+  }
+};
+
+// Up pass on the finest level (nu2 = 1): row t gets the prolonged coarse
+// correction, rows t-1 and t-2 the two half-sweeps (colours 0 and 1), and row
+// t-3, then final, the update of the iterate: u += e / s_k in float-float,
+// r_{k+1} = (f - L e) / s_k, and the sums of u_{k+1} and of r_{k+1}^2. E[j] and
+// F[j] hold row t - j; c_lo and c_hi the coarse rows around row t (t = 2I + 1:
+// rows I, I + 1; t = 2I: rows I - 1, I).
+template <int SF>
+struct UpStream {
+  LevelGeom g, gc;
+  StripLane sl;
+  const float *src;
+  const void *ue, *uc;
+  float *uh, *ul, *rn;
+  float off, scale, inv_s, omega;
+  int k;
+  P1 pxe, pxo;    // horizontal prolongation of the lane's two cells
+  bool preg[2];   // the cell's column takes the regular weights
+  float2 E[5], F[4], QF[kStreamPre], QE[kStreamPre], QH[kStreamPre], QL[kStreamPre];
+  float QC[2], c_lo, c_hi;
+  // The lane's FP32 sums of u_{k+1} and r_{k+1}^2 over its cells, in row order
+  // (so their roundings depend on the segment height, as the tiled kernels'
+  // depend on the tile shape; the iterate itself does not).
+  float su, rn2;
+
+  __device__ __forceinline__ float2 load_f(int row) const {
+    return (sl.in && row >= 0 && row < g.H)
+               ? __ldg(reinterpret_cast<const float2 *>(src + (size_t)row * g.W + sl.x))
+               : make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float2 load_e(int row) const {
+    return (sl.in && row >= 0 && row < g.H) ? s_ld2<SF>(ue, (size_t)row * g.W + sl.x)
+                                            : make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float load_c(int ci) const {
+    return (sl.in && ci >= 0 && ci < gc.H) ? s_ld(uc, (size_t)ci * gc.W + (sl.x >> 1), SF) : 0.f;
+  }
+  __device__ __forceinline__ bool stores(int row) const {
+    return sl.out && row >= sl.y0 && row < sl.y1 && row < g.H;
+  }
+  // The iterate of an output row (zero before the first cycle). Each cell is
+  // read and then written by the one lane that stores it.
+  __device__ __forceinline__ void load_u(int row, float2 &h, float2 &l) const {
+    const bool v = k > 0 && stores(row);
+    const size_t p = v ? (size_t)row * g.W + sl.x : 0;
+    h = v ? *reinterpret_cast<const float2 *>(uh + p) : make_float2(0.f, 0.f);
+    l = v ? *reinterpret_cast<const float2 *>(ul + p) : make_float2(0.f, 0.f);
+  }
+
+  // Prolongation onto row t: the regular 3/4, 1/4 weights for cells in rows
+  // [2, H - 4] and columns [2, W - 4], the general bilinear weights (first
+  // vertical, then horizontal) elsewhere; decided per cell.
+  template <int MODE, int PAR>
+  __device__ __forceinline__ void prolong(int t) {
+    const float av = PAR ? lerp_reg(c_lo, c_hi) : lerp_reg(c_hi, c_lo);
+    const float al = __shfl_up_sync(0xffffffffu, av, 1);
+    const float ar = __shfl_down_sync(0xffffffffu, av, 1);
+    if constexpr (MODE == 0) {
+      E[0].x = __fadd_rn(E[0].x, lerp_reg(av, al));
+      E[0].y = __fadd_rn(E[0].y, lerp_reg(av, ar));
+      return;
+    }
+    float bv;
+    bool rreg, tin;
+    if constexpr (MODE == 1) {  // regular rows: i1 is the farther coarse row, w1 = 1/4
+      bv = PAR ? fmaf(0.25f, __fsub_rn(c_hi, c_lo), c_lo) : fmaf(0.25f, __fsub_rn(c_lo, c_hi), c_hi);
+      rreg = tin = true;
+    } else {
+      tin = t >= 0 && t < g.H;
+      rreg = t >= 2 && t <= g.H - 4;
+      const P1 py = tin ? prolong1d(t, 0, g.H, gc.H) : P1{0, 0, 0.f};
+      const int lo_row = (t >> 1) - (PAR ? 0 : 1);
+      const float c0 = py.i0 == lo_row ? c_lo : c_hi, c1 = py.i1 == lo_row ? c_lo : c_hi;
+      bv = fmaf(py.w1, __fsub_rn(c1, c0), c0);
+    }
+    const float bl = __shfl_up_sync(0xffffffffu, bv, 1);
+    const float br = __shfl_down_sync(0xffffffffu, bv, 1);
+    if (tin && sl.in) {
+      const float ae = pxe.i1 == pxe.i0 ? bv : bl;
+      const float ao = pxo.i1 == pxo.i0 ? bv : br;
+      E[0].x = __fadd_rn(E[0].x, (rreg && preg[0]) ? lerp_reg(av, al) : fmaf(pxe.w1, __fsub_rn(ae, bv), bv));
+      E[0].y = __fadd_rn(E[0].y, (rreg && preg[1]) ? lerp_reg(av, ar) : fmaf(pxo.w1, __fsub_rn(ao, bv), bv));
+    }
+  }
+
+  template <int MODE, int PAR>
+  __device__ __forceinline__ void step(int t) {
+#pragma unroll
+    for (int j = 4; j > 0; --j) E[j] = E[j - 1];
+#pragma unroll
+    for (int j = 3; j > 0; --j) F[j] = F[j - 1];
+    const float2 qf = QF[0];
+    E[0] = QE[0];
+#pragma unroll
+    for (int j = 0; j + 1 < kStreamPre; ++j) {
+      QF[j] = QF[j + 1];
+      QE[j] = QE[j + 1];
+    }
+    QF[kStreamPre - 1] = load_f(t + kStreamPre);
+    QE[kStreamPre - 1] = load_e(t + kStreamPre);
+    const bool rin = MODE == 0 || (sl.in && t >= 0 && t < g.H);
+    F[0] = rin ? make_float2(__fmul_rn(__fsub_rn(qf.x, off), scale), __fmul_rn(__fsub_rn(qf.y, off), scale))
+               : make_float2(0.f, 0.f);
+    if constexpr (PAR == 1) {
+      c_lo = c_hi;
+      c_hi = QC[0];
+      QC[0] = QC[1];
+      QC[1] = load_c(((t + 1) >> 1) + 2);
+    }
+    prolong<MODE, PAR>(t);
+    RowMask m[4];
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int s = 1; s < 4; ++s) m[s] = row_mask(g, t - s);
+    }
+    // half-sweeps: colour 0 on row t-1, colour 1 on row t-2 (cell 1 - PAR of each)
+    constexpr int I = 1 - PAR;
+#pragma unroll
+    for (int s = 1; s <= 2; ++s) {
+      float w, e;
+      horiz<I>(E[s], w, e);
+      cell<I>(E[s]) = sl.sweep<MODE, I>(m[s], cell<I>(E[s]), w, e, cell<I>(E[s + 1]),
+                                        cell<I>(E[s - 1]), cell<I>(F[s]), omega);
+    }
+    // row t-3 is final
+    const int y = t - 3;
+    const float2 uu = E[3], n = E[4], so = E[2], f = F[3];
+    const float wl = __shfl_up_sync(0xffffffffu, uu.y, 1);
+    const float er = __shfl_down_sync(0xffffffffu, uu.x, 1);
+    float r0 = sl.res<MODE, 0>(m[3], uu.x, uu.y, wl, so.x, n.x, f.x);
+    float r1 = sl.res<MODE, 1>(m[3], uu.y, er, uu.x, so.y, n.y, f.y);
+    float2 h = QH[0], l = QL[0];
+#pragma unroll
+    for (int j = 0; j + 1 < kStreamPre; ++j) {
+      QH[j] = QH[j + 1];
+      QL[j] = QL[j + 1];
+    }
+    load_u(y + kStreamPre, QH[kStreamPre - 1], QL[kStreamPre - 1]);
+    // computed on every lane, stored (and summed) by the lanes that own row y:
+    // no branch, so the steps of a loop body schedule as one block
+    const bool st = stores(y);
+    ds_add(h.x, l.x, __fmul_rn(uu.x, inv_s));
+    ds_add(h.y, l.y, __fmul_rn(uu.y, inv_s));
+    r0 = __fmul_rn(r0, inv_s);
+    r1 = __fmul_rn(r1, inv_s);
+    su += st ? __fadd_rn(__fadd_rn(h.x, l.x), __fadd_rn(h.y, l.y)) : 0.f;
+    rn2 += st ? fmaf(r1, r1, __fmul_rn(r0, r0)) : 0.f;
+    const size_t p = st ? (size_t)y * g.W + sl.x : 0;
+    if (st) {
+      *reinterpret_cast<float2 *>(uh + p) = h;
+      *reinterpret_cast<float2 *>(ul + p) = l;
+      *reinterpret_cast<float2 *>(rn + p) = make_float2(r0, r1);
+    }
+  }
+};
+
+// Runs steps t in [tA, tE) (tE - tA even) of a stream whose first step has
+// parity P0: steps in [lo, hi) (hi - lo a multiple of U, lo of parity P0), whose
+// rows are all full, take mode MID (0 or 1), the others the general mode 2. U
+// is the stream's prefetch depth: after U steps every ring slot holds the row
+// loaded U steps earlier, so a loaded register is never copied before its use
+// (a copy would wait for the load).
+template <int P0, int MID, int U, class St>
+__device__ __forceinline__ void run_stream(St &s, int tA, int lo, int hi, int tE) {
+  constexpr int P1_ = 1 - P0;
+  static_assert(U % 2 == 0, "steps come in pairs");
+  int t = tA;
+#pragma unroll 1
+  for (; t < lo; t += 2) {
+    s.template step<2, P0>(t);
+    s.template step<2, P1_>(t + 1);
+  }
+#pragma unroll 1
+  for (; t < hi; t += U) {
+#pragma unroll
+    for (int i = 0; i < U; i += 2) {
+      s.template step<MID, P0>(t + i);
+      s.template step<MID, P1_>(t + i + 1);
+    }
+  }
+#pragma unroll 1
+  for (; t < tE; t += 2) {
+    s.template step<2, P0>(t);
+    s.template step<2, P1_>(t + 1);
+  }
+}
+
+// [lo, hi) for run_stream: the steps in [first, last), starting at a step
+// congruent to rem modulo mod (a power of two; rem of the stream's parity) and
+// trimmed to a multiple of U steps; empty (lo = hi = tE) if none.
+__device__ __forceinline__ void full_range(int tA, int tE, int first, int last, int U, int rem,
+                                           int mod, int &lo, int &hi) {
+  lo = hi = tE;
+  int l = max(tA, first);
+  l += (rem - l) & (mod - 1);
+  const int h = min(tE, last);
+  if (h - l < U) return;
+  lo = l;
+  hi = l + (h - l) / U * U;
+}
+
+template <int SF>
+__global__ void __launch_bounds__(kStreamThreads) mg0_down_stream_kernel(LvArgs a, Ctrl *ctrl, int k_in,
+                                                                        StreamGrid sg) {
+  griddep_enter();
+  if (*(volatile int *)&ctrl->stopped != 0) return;
+  DownStream<SF> d;
+  d.g = a.g;
+  d.gc = a.gc;
+  if (!strip_lane(a.g, sg, d.sl)) return;
+  const int k = cycle_index(ctrl, k_in);
+  const int c = blockIdx.z;
+  const Rhs rh = rhs_of(a, ctrl, k, c);
+  d.src = static_cast<const float *>(rh.src);
+  d.off = rh.off;
+  d.scale = rh.scale;
+  d.omega = a.omega;
+  d.fout = a.fout;
+  d.u = s_at(a.u, (size_t)c * a.g.plane, SF);
+  d.fc = s_at(a.fc, (size_t)c * a.gc.plane, SF);
+  d.rpair = 0.f;
+  const int tA = d.sl.y0 - 4, tE = d.sl.y1 + 4;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) d.E[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) d.F[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < kStreamPreDown; ++j) d.Q[j] = d.load(tA + j);
+  // full rows: t - 4 .. t in [1, H - 2]
+  int lo, hi;
+  full_range(tA, tE, 6, a.g.H - 1, kStreamPreDown, 0, 2, lo, hi);
+  if (d.sl.sx >= 1 && d.sl.sx + kStripW - 1 <= a.g.W - 2) run_stream<0, 0, kStreamPreDown>(d, tA, lo, hi, tE);
+  else run_stream<0, 1, kStreamPreDown>(d, tA, lo, hi, tE);
+}
+
+template <int SF>
+__global__ void __launch_bounds__(kStreamThreads) mg0_up_stream_kernel(LvArgs a, Ctrl *ctrl, int k_in,
+                                                                      StreamGrid sg) {
+  griddep_enter();
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, 0)) return;
+  UpStream<SF> u;
+  u.g = a.g;
+  u.gc = a.gc;
+  u.su = 0.f;
+  u.rn2 = 0.f;
+  const int c = blockIdx.z;
+  if (strip_lane(a.g, sg, u.sl)) {
+    const Rhs rh = rhs_of(a, ctrl, k, c);
+    u.src = static_cast<const float *>(rh.src);
+    u.off = rh.off;
+    u.scale = rh.scale;
+    u.inv_s = 1.f / rh.scale;  // exact: a power of two
+    u.omega = a.omega;
+    u.k = k;
+    const size_t cb = (size_t)c * a.g.plane;
+    u.ue = s_at(a.u, cb, SF);
+    u.uc = s_at(a.uc, (size_t)c * a.gc.plane, SF);
+    u.uh = a.uhi + cb;
+    u.ul = a.ulo + cb;
+    u.rn = a.rb[k & 1] + cb;
+    u.pxe = u.sl.in ? prolong1d(u.sl.x, 0, a.g.W, a.gc.W) : P1{0, 0, 0.f};
+    u.pxo = u.sl.in ? prolong1d(u.sl.x + 1, 0, a.g.W, a.gc.W) : P1{0, 0, 0.f};
+    u.preg[0] = u.sl.x >= 2 && u.sl.x <= a.g.W - 4;
+    u.preg[1] = u.sl.x + 1 >= 2 && u.sl.x + 1 <= a.g.W - 4;
+    const int tA = u.sl.y0 - 3, tE = u.sl.y1 + 3;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) u.E[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u.F[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kStreamPre; ++j) {
+      u.QF[j] = u.load_f(tA + j);
+      u.QE[j] = u.load_e(tA + j);
+      u.load_u(tA - 3 + j, u.QH[j], u.QL[j]);
+    }
+    u.c_lo = 0.f;
+    u.c_hi = u.load_c((tA - 1) >> 1);
+    u.QC[0] = u.load_c((tA + 1) >> 1);
+    u.QC[1] = u.load_c(((tA + 1) >> 1) + 1);
+    // full rows: prolongation row t in [2, H - 4], sweep and residual rows
+    // t - 3 .. t - 1 in [1, H - 2]
+    int lo, hi;
+    full_range(tA, tE, 5, a.g.H - 3, kStreamPre, 1, 2, lo, hi);
+    if (u.sl.sx >= 2 && u.sl.sx + kStripW - 1 <= a.g.W - 4) run_stream<1, 0, kStreamPre>(u, tA, lo, hi, tE);
+    else run_stream<1, 1, kStreamPre>(u, tA, lo, hi, tE);
+  }
+  double su = u.su, rn2 = u.rn2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    su += __shfl_xor_sync(0xffffffffu, su, o);
+    rn2 += __shfl_xor_sync(0xffffffffu, rn2, o);
+  }
+  __shared__ double s_part[2][kStreamThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    s_part[0][threadIdx.x >> 5] = su;
+    s_part[1][threadIdx.x >> 5] = rn2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kStreamThreads / 32; ++w) {
+      a0 += s_part[0][w];
+      a1 += s_part[1][w];
+    }
+    atomicAdd(&ctrl->sum_u[k + 1][c], a0);
+    atomicAdd(&ctrl->rnorm2[k + 1], a1);
+  }
+}
+
 // ------------------------------------------------------------------ tail: the small levels in one CTA
 //
 // Levels t..L (t the first level >= 1 with at most kTailCells cells per
@@ -1812,14 +2433,86 @@ cudaError_t launch_mg_up_t(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream
 
 inline bool small_level(const LevelGeom &g) { return g.plane < kSmallLevel; }
 
+// Streaming finest-level passes (W even, V(2, 1)); GDGS_STREAM=0 keeps the tiles.
+bool stream_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("GDGS_STREAM");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+// Output rows per segment forced by GDGS_STREAM_ROWS (rounded up to a multiple of 8), or 0.
+int stream_rows_env() {
+  static const int rows = [] {
+    const char *v = getenv("GDGS_STREAM_ROWS");
+    const int r = v ? atoi(v) : 0;
+    return r >= 1 ? (r + 7) & ~7 : 0;
+  }();
+  return rows;
+}
+
+inline bool use_stream(const LvArgs &a) { return a.level0 && a.g.W % 2 == 0 && stream_enabled(); }
+
+// Segments: the shortest height (a multiple of 8, at least 16 rows) that gives one launch at
+// most ~10.5 warps per SM. Each segment recomputes a few halo rows and starts
+// with a latency it cannot hide, so segments should be long; each warp runs its
+// rows in order, so there should be enough of them to switch between. Measured
+// best: 24 rows at 1080p (1575 warps per channel), 96 at 2160p (1587).
+StreamGrid stream_grid(const LevelGeom &g, int C) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    return n > 0 ? n : 152;
+  }();
+  StreamGrid sg;
+  sg.nstrips = (g.W + kStripOut - 1) / kStripOut;
+  const int hev = (g.H + 1) & ~1;
+  sg.S = stream_rows_env();
+  if (sg.S == 0) {
+    const long long target = (long long)sms * 21 / 2;
+    const long long nseg = std::max(1LL, target / ((long long)sg.nstrips * std::max(C, 1)));
+    const long long S = (hev + nseg - 1) / nseg;
+    sg.S = (int)std::max(16LL, (S + 7) & ~7LL);
+  }
+  sg.nseg = (hev + sg.S - 1) / sg.S;
+  return sg;
+}
+
+template <int SF>
+cudaError_t launch_stream_t(bool down, const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  const StreamGrid sg = stream_grid(a.g, C);
+  const int warps = sg.nstrips * sg.nseg;
+  const dim3 grid((warps + kStreamThreads / 32 - 1) / (kStreamThreads / 32), 1, C);
+  if (down) {
+    LaunchScope ls_(kDownName[0], st);
+    launch_k(mg0_down_stream_kernel<SF>, grid, dim3(kStreamThreads), 0, st, a, ctrl, k, sg);
+  } else {
+    LaunchScope ls_(kUpName[0], st);
+    launch_k(mg0_up_stream_kernel<SF>, grid, dim3(kStreamThreads), 0, st, a, ctrl, k, sg);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream(bool down, const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  switch (a.sf) {
+    case GDGS_STORAGE_BF16: return launch_stream_t<GDGS_STORAGE_BF16>(down, a, ctrl, k, C, st);
+    case GDGS_STORAGE_F16: return launch_stream_t<GDGS_STORAGE_F16>(down, a, ctrl, k, C, st);
+    default: return launch_stream_t<GDGS_STORAGE_F32>(down, a, ctrl, k, C, st);
+  }
+}
+
 template <int NU>
 cudaError_t launch_mg_down(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
+  if (NU == 2 && use_stream(a)) return launch_stream(true, a, ctrl, k, C, st);
   return small_level(a.g) ? launch_mg_down_t<NU, 16, 64>(a, ctrl, k, first, C, st)
                           : launch_mg_down_t<NU, 32, 128>(a, ctrl, k, first, C, st);
 }
 
 template <int NU>
 cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+  if (NU == 1 && use_stream(a)) return launch_stream(false, a, ctrl, k, C, st);
   return small_level(a.g) ? launch_mg_up_t<NU, 16, 64>(a, ctrl, k, C, st)
                           : launch_mg_up_t<NU, 32, 128>(a, ctrl, k, C, st);
 }

@@ -144,7 +144,8 @@ def test_raster_deterministic():
 # ------------------------------------------------------------------ Poisson
 
 @pytest.mark.parametrize("hw", [(64, 64), (135, 240), (17, 9), (3, 200), (1, 1), (2, 2), (100, 37),
-                                (33, 16), (270, 481)])
+                                (33, 16), (270, 481), (97, 114), (25, 58), (48, 56), (49, 2),
+                                (1, 130)])
 def test_poisson_matches_dct_oracle(hw):
     H, W = hw
     rng = np.random.default_rng(H * 1000 + W)
