@@ -1046,17 +1046,31 @@ __device__ __forceinline__ void horiz(const float2 &v, float &w, float &e) {
 // strips or segments gets the same bits in both, and the update of u and the
 // residuals of the cells next to it use one value of e.
 //
-// A full cell (all four neighbours in the grid) takes the tiled kernels'
-// interior formula; the others a masked form of the same operator, with 0/1
-// face coefficients and 1 / (number of neighbours) from a table.
+// A full cell (all four face coefficients 1) takes the tiled kernels' interior
+// formula; the others the general form of the same operator, with the face
+// coefficients of coef() and 1 / (their sum) as a correctly rounded reciprocal
+// (0 outside the grid, where a cell stays 0). On the finest level the
+// coefficients are 0 or 1; on a coarser one the cells next to a narrow last row
+// or column have others.
 
-// Finest-level cell with all four neighbours inside the grid.
-__device__ __forceinline__ bool full_row(const LevelGeom &g, int y) { return y >= 1 && y <= g.H - 2; }
-__device__ __forceinline__ bool full_col(const LevelGeom &g, int x) { return x >= 1 && x <= g.W - 2; }
+// Rows and columns whose cells have all four face coefficients 1: neighbours on
+// both sides, and none of them the narrow last cell. L0: the finest level, whose
+// cells are all full-size (its geometry constants are then known when compiling).
+template <bool L0>
+__device__ __forceinline__ bool full_row(const LevelGeom &g, int y) {
+  return y >= 1 && y <= g.H - 2 && (L0 || y <= g.H - 3 || g.lasty == 1.f);
+}
+template <bool L0>
+__device__ __forceinline__ bool full_col(const LevelGeom &g, int x) {
+  return x >= 1 && x <= g.W - 2 && (L0 || x <= g.W - 3 || g.lastx == 1.f);
+}
 
-// 1 / d for d in-grid neighbours (d = 0: a cell outside the grid, which stays 0).
-__device__ __forceinline__ float inv_count(float d) {
-  return d > 3.5f ? 0.25f : d > 2.5f ? (1.f / 3.f) : d > 1.5f ? 0.5f : d > 0.5f ? 1.f : 0.f;
+// 1 / d (0 for d = 0). On the finest level d counts neighbours (0 .. 4) and is
+// looked up; elsewhere it is a sum of face coefficients.
+template <bool L0>
+__device__ __forceinline__ float inv_sum(float d) {
+  if constexpr (L0) return d > 3.5f ? 0.25f : d > 2.5f ? (1.f / 3.f) : d > 1.5f ? 0.5f : d > 0.5f ? 1.f : 0.f;
+  else return d > 0.f ? __frcp_rn(d) : 0.f;
 }
 
 __device__ __forceinline__ float gs_fast(float old, float w, float e, float n, float s, float f,
@@ -1105,34 +1119,38 @@ __device__ __forceinline__ float lerp_reg(float near_, float far_) {
   return fmaf(0.75f, near_, __fmul_rn(0.25f, far_));
 }
 
-// Row masks of a row for the general steps.
+// Row factors of a row for the general steps: coef() of cell (y, x) is
+// e = wy ce(x), w = wy cw(x), s = wx(x) cs, n = wx(x) cn.
 struct RowMask {
-  float in, cn, cs;  // row inside the grid; north / south neighbour inside
+  float wy, cn, cs;  // cell height (0 outside the grid); north / south face parts
   bool full;
 };
 
+template <bool L0>
 __device__ __forceinline__ RowMask row_mask(const LevelGeom &g, int y) {
   RowMask r;
   const bool in = y >= 0 && y < g.H;
-  r.in = in ? 1.f : 0.f;
-  r.cn = (in && y > 0) ? 1.f : 0.f;
-  r.cs = (in && y < g.H - 1) ? 1.f : 0.f;
-  r.full = full_row(g, y);
+  const float ly = L0 ? 1.f : g.lasty, ey = L0 ? 1.f : g.ey;
+  r.wy = in ? (y == g.H - 1 ? ly : 1.f) : 0.f;
+  r.cn = (in && y > 0) ? (y == g.H - 1 ? ey : 1.f) : 0.f;
+  r.cs = (in && y + 1 < g.H) ? (y + 1 == g.H - 1 ? ey : 1.f) : 0.f;
+  r.full = full_row<L0>(g, y);
   return r;
 }
 
 // Per-warp strip and segment, the lane's pair and its column masks. Step
 // modes: 0 = rows and columns all full, 1 = rows full (column masks per lane),
 // 2 = general (row masks per row as well).
+template <bool L0>
 struct StripLane {
   int x;           // column of the lane's even cell
   bool in;         // the pair lies inside the grid (W even: both cells or neither)
   bool out;        // the lane stores its pair: a middle lane, inside the grid
   int y0, y1;      // output rows [y0, y1): y0 a multiple of 8, y1 <= H rounded up to even
   int sx;          // first column of the strip
-  float inx;       // in, as 0 / 1
-  float cw[2], ce[2];  // west / east neighbour inside, per cell
-  float invd[2];   // 1 / d of each cell in a full row
+  float wx[2];     // cell width (0 outside the grid), per cell
+  float cw[2], ce[2];  // west / east face parts, per cell (coef() in a full row)
+  float invd[2];   // 1 / (sum of the face coefficients) of each cell in a full row
   bool fcol[2];    // the cell's column is full
 
   // Smoother update of cell I of a row (row masks m used in mode 2 only).
@@ -1143,11 +1161,11 @@ struct StripLane {
     if constexpr (MODE == 0) {
       return fast;
     } else if constexpr (MODE == 1) {
-      return fcol[I] ? fast : gs_mask(old, w, e, n, s, f, cw[I], ce[I], inx, inx, invd[I], omega);
+      return fcol[I] ? fast : gs_mask(old, w, e, n, s, f, cw[I], ce[I], wx[I], wx[I], invd[I], omega);
     } else {
-      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
-      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
-      const float id = inv_count(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
+      const float cwm = __fmul_rn(cw[I], m.wy), cem = __fmul_rn(ce[I], m.wy);
+      const float cnm = __fmul_rn(m.cn, wx[I]), csm = __fmul_rn(m.cs, wx[I]);
+      const float id = inv_sum<L0>(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
       return (m.full && fcol[I]) ? fast : gs_mask(old, w, e, n, s, f, cwm, cem, cnm, csm, id, omega);
     }
   }
@@ -1160,9 +1178,9 @@ struct StripLane {
     } else if constexpr (MODE == 1) {
       return fcol[I] ? fast : gs0_mask(f, invd[I], omega);
     } else {
-      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
-      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
-      const float id = inv_count(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
+      const float cwm = __fmul_rn(cw[I], m.wy), cem = __fmul_rn(ce[I], m.wy);
+      const float cnm = __fmul_rn(m.cn, wx[I]), csm = __fmul_rn(m.cs, wx[I]);
+      const float id = inv_sum<L0>(__fadd_rn(__fadd_rn(cwm, cem), __fadd_rn(cnm, csm)));
       return (m.full && fcol[I]) ? fast : gs0_mask(f, id, omega);
     }
   }
@@ -1175,16 +1193,17 @@ struct StripLane {
     if constexpr (MODE == 0) {
       return fast;
     } else if constexpr (MODE == 1) {
-      return fcol[I] ? fast : res_mask(u, e, w, s, n, f, cw[I], ce[I], inx, inx);
+      return fcol[I] ? fast : res_mask(u, e, w, s, n, f, cw[I], ce[I], wx[I], wx[I]);
     } else {
-      const float cwm = __fmul_rn(cw[I], m.in), cem = __fmul_rn(ce[I], m.in);
-      const float cnm = __fmul_rn(m.cn, inx), csm = __fmul_rn(m.cs, inx);
+      const float cwm = __fmul_rn(cw[I], m.wy), cem = __fmul_rn(ce[I], m.wy);
+      const float cnm = __fmul_rn(m.cn, wx[I]), csm = __fmul_rn(m.cs, wx[I]);
       return (m.full && fcol[I]) ? fast : res_mask(u, e, w, s, n, f, cwm, cem, cnm, csm);
     }
   }
 };
 
-__device__ __forceinline__ bool strip_lane(const LevelGeom &g, const StreamGrid &sg, StripLane &sl) {
+template <bool L0>
+__device__ __forceinline__ bool strip_lane(const LevelGeom &g, const StreamGrid &sg, StripLane<L0> &sl) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * (kStreamThreads / 32) + (threadIdx.x >> 5);
   if (wid >= sg.nstrips * sg.nseg) return false;
@@ -1195,36 +1214,40 @@ __device__ __forceinline__ bool strip_lane(const LevelGeom &g, const StreamGrid 
   sl.out = sl.in && lane >= kStripX / 2 && lane < 32 - kStripX / 2;
   sl.y0 = seg * sg.S;
   sl.y1 = min(sl.y0 + sg.S, (g.H + 1) & ~1);
-  sl.inx = sl.in ? 1.f : 0.f;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int x = sl.x + i;
-    sl.cw[i] = (sl.in && x > 0) ? 1.f : 0.f;
-    sl.ce[i] = (sl.in && x < g.W - 1) ? 1.f : 0.f;
-    sl.invd[i] = inv_count(__fadd_rn(__fadd_rn(sl.cw[i], sl.ce[i]), __fadd_rn(sl.inx, sl.inx)));
-    sl.fcol[i] = full_col(g, x);
+    const float lx = L0 ? 1.f : g.lastx, ex = L0 ? 1.f : g.ex;
+    sl.wx[i] = sl.in ? (x == g.W - 1 ? lx : 1.f) : 0.f;
+    sl.cw[i] = (sl.in && x > 0) ? (x == g.W - 1 ? ex : 1.f) : 0.f;
+    sl.ce[i] = (sl.in && x + 1 < g.W) ? (x + 1 == g.W - 1 ? ex : 1.f) : 0.f;
+    sl.invd[i] = inv_sum<L0>(__fadd_rn(__fadd_rn(sl.cw[i], sl.ce[i]), __fadd_rn(sl.wx[i], sl.wx[i])));
+    sl.fcol[i] = full_col<L0>(g, x);
   }
   return true;
 }
 
-// Down pass on the finest level (nu1 = 2): stage 0 is the first half-sweep from
-// e = 0 on row t; stages 1-3 the next half-sweeps on rows t-1 .. t-3; row t-3 is
-// then final and stored; the residual of row t-4 is summed into the coarse
-// right-hand side. E[j] and F[j] hold row t - j of e and of the right-hand side.
-template <int SF>
+// Down pass (nu1 = 2): stage 0 is the first half-sweep from e = 0 on row t;
+// stages 1-3 the next half-sweeps on rows t-1 .. t-3; row t-3 is then final and
+// stored; the residual of row t-4 is summed into the coarse right-hand side.
+// E[j] and F[j] hold row t - j of e and of the right-hand side. L0: the finest
+// level (right-hand side r_k in FP32); otherwise the level's stored right-hand
+// side (format SF, times 4^-l).
+template <int SF, bool L0>
 struct DownStream {
   LevelGeom g, gc;
-  StripLane sl;
-  const float *src;
+  StripLane<L0> sl;
+  const void *src;
   float off, scale, omega, fout;
   void *u, *fc;
   float2 E[6], F[5], Q[kStreamPreDown];
   float rpair;
 
   __device__ __forceinline__ float2 load(int row) const {
-    return (sl.in && row >= 0 && row < g.H)
-               ? __ldg(reinterpret_cast<const float2 *>(src + (size_t)row * g.W + sl.x))
-               : make_float2(0.f, 0.f);
+    if (!(sl.in && row >= 0 && row < g.H)) return make_float2(0.f, 0.f);
+    const size_t i = (size_t)row * g.W + sl.x;
+    if constexpr (L0) return __ldg(reinterpret_cast<const float2 *>(static_cast<const float *>(src) + i));
+    else return s_ld2<SF>(src, i);
   }
 
   template <int MODE, int PAR>
@@ -1245,16 +1268,16 @@ struct DownStream {
     RowMask m[5];
     if constexpr (MODE == 2) {
 #pragma unroll
-      for (int s = 0; s < 5; ++s) m[s] = row_mask(g, t - s);
+      for (int s = 0; s < 5; ++s) m[s] = row_mask<L0>(g, t - s);
     }
     // stage 0: colour 0 of row t from zero
-    cell<I>(E[0]) = sl.sweep0<MODE, I>(m[0], cell<I>(F[0]), omega);
+    cell<I>(E[0]) = sl.template sweep0<MODE, I>(m[0], cell<I>(F[0]), omega);
     // stages 1-3: colours 1, 0, 1 of rows t-1, t-2, t-3
 #pragma unroll
     for (int s = 1; s <= 3; ++s) {
       float w, e;
       horiz<I>(E[s], w, e);
-      cell<I>(E[s]) = sl.sweep<MODE, I>(m[s], cell<I>(E[s]), w, e, cell<I>(E[s + 1]),
+      cell<I>(E[s]) = sl.template sweep<MODE, I>(m[s], cell<I>(E[s]), w, e, cell<I>(E[s + 1]),
                                         cell<I>(E[s - 1]), cell<I>(F[s]), omega);
     }
     {
@@ -1266,8 +1289,8 @@ struct DownStream {
     const float2 uu = E[4], n = E[5], so = E[3], f = F[4];
     const float wl = __shfl_up_sync(0xffffffffu, uu.y, 1);
     const float er = __shfl_down_sync(0xffffffffu, uu.x, 1);
-    const float r0 = sl.res<MODE, 0>(m[4], uu.x, uu.y, wl, so.x, n.x, f.x);
-    const float r1 = sl.res<MODE, 1>(m[4], uu.y, er, uu.x, so.y, n.y, f.y);
+    const float r0 = sl.template res<MODE, 0>(m[4], uu.x, uu.y, wl, so.x, n.x, f.x);
+    const float r1 = sl.template res<MODE, 1>(m[4], uu.y, er, uu.x, so.y, n.y, f.y);
     const float rs = __fadd_rn(r0, r1);
     if constexpr (PAR == 0) {
       rpair = rs;  // row t-4 even: the first row of a coarse row
@@ -1279,6 +1302,46 @@ struct DownStream {
   }
 };
 
+// Prolongation of the coarse correction onto row t (e0: the lane's pair of it):
+// the regular 3/4, 1/4 weights for cells in rows [2, H - 4] and columns
+// [2, W - 4], the general bilinear weights (first vertical, then horizontal)
+// elsewhere; decided per cell. c_lo, c_hi: the coarse rows around row t (t = 2I
+// + 1: rows I, I + 1; t = 2I: rows I - 1, I), in the lane's coarse column.
+template <int MODE, int PAR, bool L0>
+__device__ __forceinline__ void prolong_row(const LevelGeom &g, const LevelGeom &gc, const StripLane<L0> &sl,
+                                            const P1 &pxe, const P1 &pxo, const bool (&preg)[2],
+                                            float c_lo, float c_hi, int t, float2 &e0) {
+  const float av = PAR ? lerp_reg(c_lo, c_hi) : lerp_reg(c_hi, c_lo);
+  const float al = __shfl_up_sync(0xffffffffu, av, 1);
+  const float ar = __shfl_down_sync(0xffffffffu, av, 1);
+  if constexpr (MODE == 0) {
+    e0.x = __fadd_rn(e0.x, lerp_reg(av, al));
+    e0.y = __fadd_rn(e0.y, lerp_reg(av, ar));
+    return;
+  }
+  float bv;
+  bool rreg, tin;
+  if constexpr (MODE == 1) {  // regular rows: i1 is the farther coarse row, w1 = 1/4
+    bv = PAR ? fmaf(0.25f, __fsub_rn(c_hi, c_lo), c_lo) : fmaf(0.25f, __fsub_rn(c_lo, c_hi), c_hi);
+    rreg = tin = true;
+  } else {
+    tin = t >= 0 && t < g.H;
+    rreg = t >= 2 && t <= g.H - 4;
+    const P1 py = tin ? prolong1d(t, L0 ? 0 : g.shift, L0 ? g.H : g.H0, gc.H) : P1{0, 0, 0.f};
+    const int lo_row = (t >> 1) - (PAR ? 0 : 1);
+    const float c0 = py.i0 == lo_row ? c_lo : c_hi, c1 = py.i1 == lo_row ? c_lo : c_hi;
+    bv = fmaf(py.w1, __fsub_rn(c1, c0), c0);
+  }
+  const float bl = __shfl_up_sync(0xffffffffu, bv, 1);
+  const float br = __shfl_down_sync(0xffffffffu, bv, 1);
+  if (tin && sl.in) {
+    const float ae = pxe.i1 == pxe.i0 ? bv : bl;
+    const float ao = pxo.i1 == pxo.i0 ? bv : br;
+    e0.x = __fadd_rn(e0.x, (rreg && preg[0]) ? lerp_reg(av, al) : fmaf(pxe.w1, __fsub_rn(ae, bv), bv));
+    e0.y = __fadd_rn(e0.y, (rreg && preg[1]) ? lerp_reg(av, ar) : fmaf(pxo.w1, __fsub_rn(ao, bv), bv));
+  }
+}
+
 // Up pass on the finest level (nu2 = 1): row t gets the prolonged coarse
 // correction, rows t-1 and t-2 the two half-sweeps (colours 0 and 1), and row
 // t-3, then final, the update of the iterate: u += e / s_k in float-float,
@@ -1288,7 +1351,8 @@ struct DownStream {
 template <int SF>
 struct UpStream {
   LevelGeom g, gc;
-  StripLane sl;
+  static constexpr bool L0 = true;
+  StripLane<true> sl;
   const float *src;
   const void *ue, *uc;
   float *uh, *ul, *rn;
@@ -1327,42 +1391,6 @@ struct UpStream {
     l = v ? *reinterpret_cast<const float2 *>(ul + p) : make_float2(0.f, 0.f);
   }
 
-  // Prolongation onto row t: the regular 3/4, 1/4 weights for cells in rows
-  // [2, H - 4] and columns [2, W - 4], the general bilinear weights (first
-  // vertical, then horizontal) elsewhere; decided per cell.
-  template <int MODE, int PAR>
-  __device__ __forceinline__ void prolong(int t) {
-    const float av = PAR ? lerp_reg(c_lo, c_hi) : lerp_reg(c_hi, c_lo);
-    const float al = __shfl_up_sync(0xffffffffu, av, 1);
-    const float ar = __shfl_down_sync(0xffffffffu, av, 1);
-    if constexpr (MODE == 0) {
-      E[0].x = __fadd_rn(E[0].x, lerp_reg(av, al));
-      E[0].y = __fadd_rn(E[0].y, lerp_reg(av, ar));
-      return;
-    }
-    float bv;
-    bool rreg, tin;
-    if constexpr (MODE == 1) {  // regular rows: i1 is the farther coarse row, w1 = 1/4
-      bv = PAR ? fmaf(0.25f, __fsub_rn(c_hi, c_lo), c_lo) : fmaf(0.25f, __fsub_rn(c_lo, c_hi), c_hi);
-      rreg = tin = true;
-    } else {
-      tin = t >= 0 && t < g.H;
-      rreg = t >= 2 && t <= g.H - 4;
-      const P1 py = tin ? prolong1d(t, 0, g.H, gc.H) : P1{0, 0, 0.f};
-      const int lo_row = (t >> 1) - (PAR ? 0 : 1);
-      const float c0 = py.i0 == lo_row ? c_lo : c_hi, c1 = py.i1 == lo_row ? c_lo : c_hi;
-      bv = fmaf(py.w1, __fsub_rn(c1, c0), c0);
-    }
-    const float bl = __shfl_up_sync(0xffffffffu, bv, 1);
-    const float br = __shfl_down_sync(0xffffffffu, bv, 1);
-    if (tin && sl.in) {
-      const float ae = pxe.i1 == pxe.i0 ? bv : bl;
-      const float ao = pxo.i1 == pxo.i0 ? bv : br;
-      E[0].x = __fadd_rn(E[0].x, (rreg && preg[0]) ? lerp_reg(av, al) : fmaf(pxe.w1, __fsub_rn(ae, bv), bv));
-      E[0].y = __fadd_rn(E[0].y, (rreg && preg[1]) ? lerp_reg(av, ar) : fmaf(pxo.w1, __fsub_rn(ao, bv), bv));
-    }
-  }
-
   template <int MODE, int PAR>
   __device__ __forceinline__ void step(int t) {
 #pragma unroll
@@ -1387,11 +1415,11 @@ struct UpStream {
       QC[0] = QC[1];
       QC[1] = load_c(((t + 1) >> 1) + 2);
     }
-    prolong<MODE, PAR>(t);
+    prolong_row<MODE, PAR, L0>(g, gc, sl, pxe, pxo, preg, c_lo, c_hi, t, E[0]);
     RowMask m[4];
     if constexpr (MODE == 2) {
 #pragma unroll
-      for (int s = 1; s < 4; ++s) m[s] = row_mask(g, t - s);
+      for (int s = 1; s < 4; ++s) m[s] = row_mask<L0>(g, t - s);
     }
     // half-sweeps: colour 0 on row t-1, colour 1 on row t-2 (cell 1 - PAR of each)
     constexpr int I = 1 - PAR;
@@ -1431,6 +1459,72 @@ struct UpStream {
       *reinterpret_cast<float2 *>(ul + p) = l;
       *reinterpret_cast<float2 *>(rn + p) = make_float2(r0, r1);
     }
+  }
+};
+
+// Up pass on a level l >= 1 (nu2 = 1): row t gets the prolonged coarse
+// correction, rows t-1 and t-2 the two half-sweeps (colours 0 and 1); row t-2 is
+// then final and stored (format SF) to the level's up-pass array. E[j] and F[j]
+// hold row t - j; c_lo and c_hi as in UpStream.
+template <int SF>
+struct UpStreamC {
+  LevelGeom g, gc;
+  static constexpr bool L0 = false;
+  StripLane<false> sl;
+  const void *src, *ue, *uc;
+  void *uo;
+  float scale, omega;
+  P1 pxe, pxo;
+  bool preg[2];
+  float2 E[4], F[3], QF[kStreamPre], QE[kStreamPre];
+  float QC[2], c_lo, c_hi;
+
+  __device__ __forceinline__ float2 load2(const void *p, int row) const {
+    return (sl.in && row >= 0 && row < g.H) ? s_ld2<SF>(p, (size_t)row * g.W + sl.x)
+                                            : make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float load_c(int ci) const {
+    return (sl.in && ci >= 0 && ci < gc.H) ? s_ld(uc, (size_t)ci * gc.W + (sl.x >> 1), SF) : 0.f;
+  }
+
+  template <int MODE, int PAR>
+  __device__ __forceinline__ void step(int t) {
+#pragma unroll
+    for (int j = 3; j > 0; --j) E[j] = E[j - 1];
+#pragma unroll
+    for (int j = 2; j > 0; --j) F[j] = F[j - 1];
+    const float2 qf = QF[0];
+    E[0] = QE[0];
+#pragma unroll
+    for (int j = 0; j + 1 < kStreamPre; ++j) {
+      QF[j] = QF[j + 1];
+      QE[j] = QE[j + 1];
+    }
+    QF[kStreamPre - 1] = load2(src, t + kStreamPre);
+    QE[kStreamPre - 1] = load2(ue, t + kStreamPre);
+    F[0] = make_float2(__fmul_rn(qf.x, scale), __fmul_rn(qf.y, scale));
+    if constexpr (PAR == 1) {
+      c_lo = c_hi;
+      c_hi = QC[0];
+      QC[0] = QC[1];
+      QC[1] = load_c(((t + 1) >> 1) + 2);
+    }
+    prolong_row<MODE, PAR, L0>(g, gc, sl, pxe, pxo, preg, c_lo, c_hi, t, E[0]);
+    RowMask m[3];
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int s = 1; s < 3; ++s) m[s] = row_mask<L0>(g, t - s);
+    }
+    constexpr int I = 1 - PAR;
+#pragma unroll
+    for (int s = 1; s <= 2; ++s) {
+      float w, e;
+      horiz<I>(E[s], w, e);
+      cell<I>(E[s]) = sl.sweep<MODE, I>(m[s], cell<I>(E[s]), w, e, cell<I>(E[s + 1]),
+                                        cell<I>(E[s - 1]), cell<I>(F[s]), omega);
+    }
+    const int y = t - 2;
+    if (sl.out && y >= sl.y0 && y < sl.y1 && y < g.H) s_st2<SF>(uo, (size_t)y * g.W + sl.x, E[2]);
   }
 };
 
@@ -1479,19 +1573,25 @@ __device__ __forceinline__ void full_range(int tA, int tE, int first, int last, 
   hi = l + (h - l) / U * U;
 }
 
-template <int SF>
-__global__ void __launch_bounds__(kStreamThreads) mg0_down_stream_kernel(LvArgs a, Ctrl *ctrl, int k_in,
-                                                                        StreamGrid sg) {
+// Last row (exclusive) of the full rows: H - 1, or H - 2 when the last row is narrow.
+template <bool L0>
+__device__ __forceinline__ int full_row_end(const LevelGeom &g) { return (L0 || g.lasty == 1.f) ? g.H - 1 : g.H - 2; }
+template <bool L0>
+__device__ __forceinline__ int full_col_end(const LevelGeom &g) { return (L0 || g.lastx == 1.f) ? g.W - 1 : g.W - 2; }
+
+template <int SF, bool L0>
+__global__ void __launch_bounds__(kStreamThreads) mg_down_stream_kernel(LvArgs a, Ctrl *ctrl, int k_in,
+                                                                       int first, StreamGrid sg) {
   griddep_enter();
-  if (*(volatile int *)&ctrl->stopped != 0) return;
-  DownStream<SF> d;
+  const int k = cycle_index(ctrl, k_in);
+  if (L0 ? *(volatile int *)&ctrl->stopped != 0 : should_stop(ctrl, k, first)) return;
+  DownStream<SF, L0> d;
   d.g = a.g;
   d.gc = a.gc;
   if (!strip_lane(a.g, sg, d.sl)) return;
-  const int k = cycle_index(ctrl, k_in);
   const int c = blockIdx.z;
   const Rhs rh = rhs_of(a, ctrl, k, c);
-  d.src = static_cast<const float *>(rh.src);
+  d.src = rh.src;
   d.off = rh.off;
   d.scale = rh.scale;
   d.omega = a.omega;
@@ -1506,11 +1606,56 @@ __global__ void __launch_bounds__(kStreamThreads) mg0_down_stream_kernel(LvArgs 
   for (int j = 0; j < 5; ++j) d.F[j] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < kStreamPreDown; ++j) d.Q[j] = d.load(tA + j);
-  // full rows: t - 4 .. t in [1, H - 2]
+  // full rows t - 4 .. t
   int lo, hi;
-  full_range(tA, tE, 6, a.g.H - 1, kStreamPreDown, 0, 2, lo, hi);
-  if (d.sl.sx >= 1 && d.sl.sx + kStripW - 1 <= a.g.W - 2) run_stream<0, 0, kStreamPreDown>(d, tA, lo, hi, tE);
+  full_range(tA, tE, 6, full_row_end<L0>(a.g), kStreamPreDown, 0, 2, lo, hi);
+  if (d.sl.sx >= 1 && d.sl.sx + kStripW <= full_col_end<L0>(a.g)) run_stream<0, 0, kStreamPreDown>(d, tA, lo, hi, tE);
   else run_stream<0, 1, kStreamPreDown>(d, tA, lo, hi, tE);
+}
+
+template <int SF>
+__global__ void __launch_bounds__(kStreamThreads) mg_upc_stream_kernel(LvArgs a, Ctrl *ctrl, int k_in,
+                                                                      StreamGrid sg) {
+  griddep_enter();
+  const int k = cycle_index(ctrl, k_in);
+  if (should_stop(ctrl, k, 0)) return;
+  UpStreamC<SF> u;
+  u.g = a.g;
+  u.gc = a.gc;
+  if (!strip_lane(a.g, sg, u.sl)) return;
+  const int c = blockIdx.z;
+  const Rhs rh = rhs_of(a, ctrl, k, c);
+  u.src = rh.src;
+  u.scale = rh.scale;
+  u.omega = a.omega;
+  u.ue = s_at(a.u, (size_t)c * a.g.plane, SF);
+  u.uc = s_at(a.uc, (size_t)c * a.gc.plane, SF);
+  u.uo = s_at(a.uo, (size_t)c * a.g.plane, SF);
+  u.pxe = u.sl.in ? prolong1d(u.sl.x, a.g.shift, a.g.W0, a.gc.W) : P1{0, 0, 0.f};
+  u.pxo = u.sl.in ? prolong1d(u.sl.x + 1, a.g.shift, a.g.W0, a.gc.W) : P1{0, 0, 0.f};
+  u.preg[0] = u.sl.x >= 2 && u.sl.x <= a.g.W - 4;
+  u.preg[1] = u.sl.x + 1 >= 2 && u.sl.x + 1 <= a.g.W - 4;
+  const int tA = u.sl.y0 - 2, tE = u.sl.y1 + 2;  // even: the first step has parity 0
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u.E[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) u.F[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < kStreamPre; ++j) {
+    u.QF[j] = u.load2(u.src, tA + j);
+    u.QE[j] = u.load2(u.ue, tA + j);
+  }
+  // t = tA = 2I: coarse rows I - 1, I in use, I + 1 and I + 2 loaded ahead
+  const int I0 = tA >> 1;
+  u.c_lo = u.load_c(I0 - 1);
+  u.c_hi = u.load_c(I0);
+  u.QC[0] = u.load_c(I0 + 1);
+  u.QC[1] = u.load_c(I0 + 2);
+  // full rows: prolongation row t in [2, H - 4], sweep rows t - 2, t - 1 full
+  int lo, hi;
+  full_range(tA, tE, 4, a.g.H - 3, kStreamPre, 0, 2, lo, hi);
+  if (u.sl.sx >= 2 && u.sl.sx + kStripW - 1 <= a.g.W - 4) run_stream<0, 0, kStreamPre>(u, tA, lo, hi, tE);
+  else run_stream<0, 1, kStreamPre>(u, tA, lo, hi, tE);
 }
 
 template <int SF>
@@ -2452,7 +2597,23 @@ int stream_rows_env() {
   return rows;
 }
 
-inline bool use_stream(const LvArgs &a) { return a.level0 && a.g.W % 2 == 0 && stream_enabled(); }
+// Levels 0 .. n-1 stream their down passes (GDGS_STREAM_DOWN_LEVELS, else 1) and
+// their up passes (GDGS_STREAM_UP_LEVELS, else 3), each if its width is even.
+int stream_levels(bool down) {
+  static const int nd = [] {
+    const char *v = getenv("GDGS_STREAM_DOWN_LEVELS");
+    return v ? std::max(1, atoi(v)) : 1;
+  }();
+  static const int nu = [] {
+    const char *v = getenv("GDGS_STREAM_UP_LEVELS");
+    return v ? std::max(1, atoi(v)) : 3;
+  }();
+  return down ? nd : nu;
+}
+
+inline bool use_stream(const LvArgs &a, bool down) {
+  return a.g.W % 2 == 0 && a.g.shift < stream_levels(down) && stream_enabled();
+}
 
 // Segments: the shortest height (a multiple of 8, at least 16 rows) that gives one launch at
 // most ~10.5 warps per SM. Each segment recomputes a few halo rows and starts
@@ -2481,38 +2642,41 @@ StreamGrid stream_grid(const LevelGeom &g, int C) {
 }
 
 template <int SF>
-cudaError_t launch_stream_t(bool down, const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+cudaError_t launch_stream_t(bool down, const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
   const StreamGrid sg = stream_grid(a.g, C);
   const int warps = sg.nstrips * sg.nseg;
   const dim3 grid((warps + kStreamThreads / 32 - 1) / (kStreamThreads / 32), 1, C);
+  const dim3 block(kStreamThreads);
   if (down) {
-    LaunchScope ls_(kDownName[0], st);
-    launch_k(mg0_down_stream_kernel<SF>, grid, dim3(kStreamThreads), 0, st, a, ctrl, k, sg);
+    LaunchScope ls_(kDownName[a.g.shift], st);
+    if (a.level0) launch_k(mg_down_stream_kernel<SF, true>, grid, block, 0, st, a, ctrl, k, first, sg);
+    else launch_k(mg_down_stream_kernel<SF, false>, grid, block, 0, st, a, ctrl, k, first, sg);
   } else {
-    LaunchScope ls_(kUpName[0], st);
-    launch_k(mg0_up_stream_kernel<SF>, grid, dim3(kStreamThreads), 0, st, a, ctrl, k, sg);
+    LaunchScope ls_(kUpName[a.g.shift], st);
+    if (a.level0) launch_k(mg0_up_stream_kernel<SF>, grid, block, 0, st, a, ctrl, k, sg);
+    else launch_k(mg_upc_stream_kernel<SF>, grid, block, 0, st, a, ctrl, k, sg);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream(bool down, const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
+cudaError_t launch_stream(bool down, const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
   switch (a.sf) {
-    case GDGS_STORAGE_BF16: return launch_stream_t<GDGS_STORAGE_BF16>(down, a, ctrl, k, C, st);
-    case GDGS_STORAGE_F16: return launch_stream_t<GDGS_STORAGE_F16>(down, a, ctrl, k, C, st);
-    default: return launch_stream_t<GDGS_STORAGE_F32>(down, a, ctrl, k, C, st);
+    case GDGS_STORAGE_BF16: return launch_stream_t<GDGS_STORAGE_BF16>(down, a, ctrl, k, first, C, st);
+    case GDGS_STORAGE_F16: return launch_stream_t<GDGS_STORAGE_F16>(down, a, ctrl, k, first, C, st);
+    default: return launch_stream_t<GDGS_STORAGE_F32>(down, a, ctrl, k, first, C, st);
   }
 }
 
 template <int NU>
 cudaError_t launch_mg_down(const LvArgs &a, Ctrl *ctrl, int k, int first, int C, cudaStream_t st) {
-  if (NU == 2 && use_stream(a)) return launch_stream(true, a, ctrl, k, C, st);
+  if (NU == 2 && use_stream(a, true)) return launch_stream(true, a, ctrl, k, first, C, st);
   return small_level(a.g) ? launch_mg_down_t<NU, 16, 64>(a, ctrl, k, first, C, st)
                           : launch_mg_down_t<NU, 32, 128>(a, ctrl, k, first, C, st);
 }
 
 template <int NU>
 cudaError_t launch_mg_up(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream_t st) {
-  if (NU == 1 && use_stream(a)) return launch_stream(false, a, ctrl, k, C, st);
+  if (NU == 1 && use_stream(a, false)) return launch_stream(false, a, ctrl, k, 0, C, st);
   return small_level(a.g) ? launch_mg_up_t<NU, 16, 64>(a, ctrl, k, C, st)
                           : launch_mg_up_t<NU, 32, 128>(a, ctrl, k, C, st);
 }
