@@ -17,11 +17,14 @@
 // exponent already puts them below alpha_min (with a 1e-3 margin in the
 // exponent) are skipped without the exponential.
 //
-// A warp holds two pixel rows of the tile. When a batch is staged, every splat
-// also gets the mask of the warps whose rows its ellipse can reach (closed form,
-// with the binning's margins), and each warp compacts the batch into a list of
-// its own in front-to-back order, so a warp never evaluates a splat that cannot
-// reach its rows (they would all have been skipped by the exponent test).
+// A warp holds a 4 x 8 pixel block of the tile (warp w: rows 4 (w >> 1) .. +3,
+// columns 8 (w & 1) .. +7). When a batch is staged, every splat also gets the
+// mask of the warps whose blocks its ellipse's bounding box can reach (closed
+// form, with the binning's margins), and each warp compacts the batch into a
+// list of its own in front-to-back order, so a warp never evaluates a splat that
+// cannot reach its block (it would have been skipped by the exponent test at
+// every pixel there). A compact block is reached by fewer of the small splats
+// than a strip of two full rows.
 #include "gdgs_internal.cuh"
 
 namespace gdgs {
@@ -34,22 +37,30 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Warps whose two pixel rows the splat's ellipse p2 <= log2(opacity / alpha_min)
-// + 1e-3 (the exponent cut of the composite) can reach, widened like the
-// binning's cut (0.1 % + 0.01) so that no reachable row is dropped. The
-// ellipse's vertical half-extent is sqrt(lim 4A / (4AC - B'^2)) around the
-// centre h_y + l_y (tile-relative rows; pixel row r has its centre at r + 0.5).
-__device__ __forceinline__ uint8_t warp_rows_mask(const StagedSplat &st, float4 k, float amin) {
+// Warps whose 4 x 8 pixel blocks the bounding box of the splat's ellipse p2 <=
+// log2(opacity / alpha_min) + 1e-3 (the exponent cut of the composite) can
+// reach, widened like the binning's cut (0.1 % + 0.01) so that no reachable
+// pixel is dropped. The ellipse's half-extents are sqrt(lim 4A / D) vertically
+// and sqrt(lim 4C / D) horizontally, D = 4AC - B'^2, around the tile-relative
+// centre (h_x + l_x, h_y + l_y); pixel (c, r) has its centre at (c + 0.5, r + 0.5).
+__device__ __forceinline__ uint8_t warp_block_mask(const StagedSplat &st, float4 k, float amin) {
   const float A = k.x, B = k.y, C = k.z;
   const float lim = (log2f(k.w / amin) + 1e-3f) * 1.001f + 0.01f;
   const float D = fmaf(4.f * A, C, -B * B);
   if (!(lim > 0.f) || !(D > 0.f)) return 0xffu;  // degenerate: keep for every warp
   const float hy = sqrtf(lim * 4.f * A / D) * 1.0001f + 1e-3f;
-  const float cy = st.geo.y + st.ly;
+  const float hx = sqrtf(lim * 4.f * C / D) * 1.0001f + 1e-3f;
+  const float cy = st.geo.y + st.ly, cx = st.geo.x + st.lx;
   const float r0 = ceilf(cy - hy - 0.5f), r1 = floorf(cy + hy - 0.5f);  // reachable pixel rows
-  if (!(r1 >= 0.f) || !(r0 <= (float)(kTile - 1))) return 0u;
-  const int i0 = max(0, (int)r0) >> 1, i1 = min(kTile - 1, (int)r1) >> 1;
-  return (uint8_t)(((2u << i1) - 1u) & ~((1u << i0) - 1u));
+  const float c0 = ceilf(cx - hx - 0.5f), c1 = floorf(cx + hx - 0.5f);  // and columns
+  if (!(r1 >= 0.f) || !(r0 <= (float)(kTile - 1)) || !(c1 >= 0.f) || !(c0 <= (float)(kTile - 1)))
+    return 0u;
+  const int i0 = max(0, (int)r0) >> 2, i1 = min(kTile - 1, (int)r1) >> 2;  // row blocks 0..3
+  const int j0 = max(0, (int)c0) >> 3, j1 = min(kTile - 1, (int)c1) >> 3;  // column blocks 0..1
+  const unsigned rows = ((2u << i1) - 1u) & ~((1u << i0) - 1u);
+  // row block i -> warps 2i (left block) and 2i + 1 (right block)
+  const unsigned even = (rows & 1u) | ((rows & 2u) << 1) | ((rows & 4u) << 2) | ((rows & 8u) << 3);
+  return (uint8_t)((j0 == 0 ? even : 0u) | (j1 == 1 ? even << 1 : 0u));
 }
 
 template <int Q>
@@ -69,7 +80,7 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
   const int tile = a.use_active ? (int)a.active[blockIdx.x] : (int)blockIdx.x;
   const int tyi = tile / a.tiles_x, txi = tile - tyi * a.tiles_x;
   const int x0 = txi * kTile, y0 = tyi * kTile;
-  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int lx = 8 * (warp & 1) + (lane & 7), ly = 4 * (warp >> 1) + (lane >> 3);
   const int px = x0 + lx, py = y0 + ly;
   const bool inside = px < a.W && py < a.H;
   const float fpx = lx + 0.5f, fpy = ly + 0.5f;
@@ -93,7 +104,7 @@ __global__ void __launch_bounds__(256) raster_kernel(RasterArgs a) {
       const StagedSplat st = stage_splat(a.smean[g], kc, x0f, y0f);
       s_geo[threadIdx.x] = st.geo;
       s_geo2[threadIdx.x] = st.geo2;
-      s_wmask[threadIdx.x] = warp_rows_mask(st, kc, amin);
+      s_wmask[threadIdx.x] = warp_block_mask(st, kc, amin);
       const float *gp = a.grad + (size_t)g * Q;
       float gv[QV * 4];
 #pragma unroll
