@@ -14,8 +14,9 @@
 // Compared with a 64-bit (tile | depth) key this sorts 13 instead of 45 bits per
 // pair and moves 8 instead of 12 bytes per pair and pass.
 //
-// The radix sort is a classic three-kernel LSD pass (block histograms, one scan
-// over digit-major histograms, stable scatter). Ranking inside a block is
+// The radix sort is a classic LSD pass in three kernels (block histograms, one
+// scan over digit-major histograms, stable scatter, which also scans the 256
+// digit totals into the digit bases). Ranking inside a block is
 // stable: items are taken in rounds of 256 consecutive keys; within a warp peers
 // of a digit are found with __match_any_sync and ranked by lane; warps are
 // ranked in order through a shared-memory prefix per digit.
@@ -104,23 +105,16 @@ radix_scan_digit_kernel(uint32_t *hist, uint32_t *tot, const unsigned long long 
   if (threadIdx.x == 0) tot[blockIdx.x] = run;
 }
 
-// Exclusive scan of the digit totals into the digit bases (in place).
-__global__ void __launch_bounds__(256) radix_scan_top_kernel(uint32_t *tot, unsigned ndig) {
-  griddep_enter();
-  const unsigned v = threadIdx.x < ndig ? tot[threadIdx.x] : 0u;
-  unsigned t;
-  const unsigned ex = scan256(v, &t);
-  if (threadIdx.x < ndig) tot[threadIdx.x] = ex;
-}
-
 // keys_next (nullable): the key written out for element i is keys_next[i]
 // instead of the key ranked on, so a first pass over a secondary key leaves the
-// primary keys in its order for the passes that follow.
+// primary keys in its order for the passes that follow. dtot: the digit totals;
+// every block scans them into the digit bases itself (256 values: cheaper than a
+// launch).
 template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                      uint32_t *vals_out, const unsigned long long *n_dev, unsigned cap, int shift,
-                     unsigned mask, const uint32_t *hist, const uint32_t *dbase,
+                     unsigned mask, const uint32_t *hist, const uint32_t *dtot,
                      const uint32_t *keys_next) {
   griddep_enter();
   constexpr int kWarps = kRadixThreads / 32;
@@ -130,7 +124,11 @@ radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t 
   const unsigned nb = (n + kRadixThreads * ITEMS - 1) / (kRadixThreads * ITEMS);
   if (blockIdx.x >= nb) return;
   const int w = threadIdx.x >> 5;
-  if (threadIdx.x <= mask) run[threadIdx.x] = dbase[threadIdx.x] + hist[threadIdx.x * nb + blockIdx.x];
+  {
+    unsigned all;
+    const unsigned dbase = scan256(threadIdx.x <= mask ? dtot[threadIdx.x] : 0u, &all);
+    if (threadIdx.x <= mask) run[threadIdx.x] = dbase + hist[threadIdx.x * nb + blockIdx.x];
+  }
   const unsigned base = blockIdx.x * (kRadixThreads * ITEMS);
   for (int r = 0; r < ITEMS; ++r) {
     const unsigned i = base + r * kRadixThreads + threadIdx.x;
@@ -399,7 +397,6 @@ cudaError_t radix_pass(const uint32_t *ki, const uint32_t *vi, uint32_t *ko, uin
   { LaunchScope ls_("radix_hist", st); launch_k(radix_hist_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, n_dev, cap, shift, mask, hist); }
   uint32_t *dtot = hist + (size_t)256 * blocks;
   { LaunchScope ls_("radix_scan", st); launch_k(radix_scan_digit_kernel<ITEMS>, mask + 1, 256, 0, st, hist, dtot, n_dev, cap); }
-  { LaunchScope ls_("radix_scan_top", st); launch_k(radix_scan_top_kernel, 1, 256, 0, st, dtot, mask + 1); }
   {
     LaunchScope ls_("radix_scatter", st);
     launch_k(radix_scatter_kernel<ITEMS>, blocks, kRadixThreads, 0, st, ki, vi, ko, vo, n_dev, cap,
