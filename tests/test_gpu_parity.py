@@ -145,7 +145,7 @@ def test_raster_deterministic():
 
 @pytest.mark.parametrize("hw", [(64, 64), (135, 240), (17, 9), (3, 200), (1, 1), (2, 2), (100, 37),
                                 (33, 16), (270, 481), (97, 114), (25, 58), (48, 56), (49, 2),
-                                (1, 130)])
+                                (1, 130), (99, 203), (61, 483)])
 def test_poisson_matches_dct_oracle(hw):
     H, W = hw
     rng = np.random.default_rng(H * 1000 + W)
