@@ -80,13 +80,16 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
   __shared__ float s_opa[256];
   __shared__ float s_g[Q][256];
   __shared__ uint32_t s_id[256];
+  __shared__ uint8_t s_wmask[256];    // warps each staged splat can reach (as the forward)
+  __shared__ uint8_t s_list[8][256];  // per warp: the batch's splats that can reach it
   __shared__ int s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ntiles = a.ctrl->n_active;
   if (blockIdx.x >= ntiles) return;
   const int tile = (int)a.active[blockIdx.x];
   const int tyi = tile / a.tiles_x, txi = tile - tyi * a.tiles_x;
   const int x0 = txi * kTile, y0 = tyi * kTile;
-  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int lx = 8 * (warp & 1) + (lane & 7), ly = 4 * (warp >> 1) + (lane >> 3);  // 4 x 8 blocks
   const int px = x0 + lx, py = y0 + ly;
   const bool inside = px < a.W && py < a.H;
   const float fpx = lx + 0.5f, fpy = ly + 0.5f;
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
       s_l[threadIdx.x] = make_float2(st.lx, st.ly);
       s_opa[threadIdx.x] = k.w;
       s_id[threadIdx.x] = g;
+      s_wmask[threadIdx.x] = warp_block_mask(st, k, amin);
 #pragma unroll
       for (int q = 0; q < Q; ++q) s_g[q][threadIdx.x] = a.attr[(size_t)g * Q + q];
     }
@@ -123,8 +127,10 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
     stage(s);
     __syncthreads();
     const int cnt = min(256u, rg.y - s);
+    const int nl = warp_list(s_wmask, cnt, s_list[warp], warp, lane);
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
+      for (int i = 0; i < nl; ++i) {
+        const int k = s_list[warp][i];
         const float4 ge = s_geo[k];
         const float4 ge2 = s_geo2[k];
         float X, Y;
@@ -154,14 +160,16 @@ __global__ void __launch_bounds__(256) raster_backward_kernel(RasterBwdArgs a) {
   float B[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) B[q] = 0.f;
-  const int lane = threadIdx.x & 31;
   const unsigned first_batch = rg.x + (unsigned)(jmax - (int)rg.x) / 256u * 256u;
   for (int s = (int)first_batch; s >= (int)rg.x; s -= 256) {
     __syncthreads();
     stage((unsigned)s);
     __syncthreads();
     const int cnt = min(256, (int)rg.y - s);
-    for (int k = min(cnt - 1, jmax - s); k >= 0; --k) {
+    const int nl = warp_list(s_wmask, cnt, s_list[warp], warp, lane);
+    for (int i = nl - 1; i >= 0; --i) {
+      const int k = s_list[warp][i];
+      if (k > jmax - s) continue;  // after the tile's last contributing splat
       const int j = s + k;
       float v[6 + Q];
 #pragma unroll

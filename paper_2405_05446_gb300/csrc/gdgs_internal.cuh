@@ -264,6 +264,49 @@ __device__ __forceinline__ float staged_exponent(const float4 &ge, const float4 
   return fmaf(X, fmaf(ge.z, X, fmaf(ge.w, Y, ge2.z)), Y * fmaf(ge2.x, Y, ge2.w));
 }
 
+// Rasterisers: a warp holds a 4 x 8 pixel block of a 16 x 16 tile (warp w: rows
+// 4 (w >> 1) .. +3, columns 8 (w & 1) .. +7). Warps whose 4 x 8 pixel blocks the bounding box of the splat's ellipse p2 <=
+// log2(opacity / alpha_min) + 1e-3 (the exponent cut of the composite) can
+// reach, widened like the binning's cut (0.1 % + 0.01) so that no reachable
+// pixel is dropped. The ellipse's half-extents are sqrt(lim 4A / D) vertically
+// and sqrt(lim 4C / D) horizontally, D = 4AC - B'^2, around the tile-relative
+// centre (h_x + l_x, h_y + l_y); pixel (c, r) has its centre at (c + 0.5, r + 0.5).
+__device__ __forceinline__ uint8_t warp_block_mask(const StagedSplat &st, float4 k, float amin) {
+  const float A = k.x, B = k.y, C = k.z;
+  const float lim = (log2f(k.w / amin) + 1e-3f) * 1.001f + 0.01f;
+  const float D = fmaf(4.f * A, C, -B * B);
+  if (!(lim > 0.f) || !(D > 0.f)) return 0xffu;  // degenerate: keep for every warp
+  const float hy = sqrtf(lim * 4.f * A / D) * 1.0001f + 1e-3f;
+  const float hx = sqrtf(lim * 4.f * C / D) * 1.0001f + 1e-3f;
+  const float cy = st.geo.y + st.ly, cx = st.geo.x + st.lx;
+  const float r0 = ceilf(cy - hy - 0.5f), r1 = floorf(cy + hy - 0.5f);  // reachable pixel rows
+  const float c0 = ceilf(cx - hx - 0.5f), c1 = floorf(cx + hx - 0.5f);  // and columns
+  if (!(r1 >= 0.f) || !(r0 <= (float)(kTile - 1)) || !(c1 >= 0.f) || !(c0 <= (float)(kTile - 1)))
+    return 0u;
+  const int i0 = max(0, (int)r0) >> 2, i1 = min(kTile - 1, (int)r1) >> 2;  // row blocks 0..3
+  const int j0 = max(0, (int)c0) >> 3, j1 = min(kTile - 1, (int)c1) >> 3;  // column blocks 0..1
+  const unsigned rows = ((2u << i1) - 1u) & ~((1u << i0) - 1u);
+  // row block i -> warps 2i (left block) and 2i + 1 (right block)
+  const unsigned even = (rows & 1u) | ((rows & 2u) << 1) | ((rows & 4u) << 2) | ((rows & 8u) << 3);
+  return (uint8_t)((j0 == 0 ? even : 0u) | (j1 == 1 ? even << 1 : 0u));
+}
+
+// The batch entries (of cnt) whose mask includes this warp, compacted in batch
+// order into list; returns their number. Called by all 32 lanes of the warp.
+__device__ __forceinline__ int warp_list(const uint8_t *wmask, int cnt, uint8_t *list, int warp,
+                                         int lane) {
+  int nl = 0;
+  for (int k0 = 0; k0 < cnt; k0 += 32) {
+    const int k = k0 + lane;
+    const bool in = k < cnt && ((wmask[k] >> warp) & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, in);
+    if (in) list[nl + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
+    nl += __popc(b);
+  }
+  __syncwarp();
+  return nl;
+}
+
 struct RasterArgs {
   const float4 *smean, *sconic;
   const float *grad;
