@@ -3026,6 +3026,25 @@ cudaError_t fork_set(cudaStream_t st, ForkSet **out) {
   return cudaSuccess;
 }
 
+// Blocks per channel of the four-pixel passes (256 threads, a grid-stride loop
+// over quads): a fixed count, 8/3 per SM (eight CTAs per SM for three channels).
+// Each block ends in FP64 atomics on per-channel (or one) addresses, so a block
+// per 256 quads (thousands of atomics on one address) serialised at the end; and
+// the count does not depend on the number of channels, so a channel's sums (and
+// with them its solve) come out the same bits whether it is solved alone or with
+// others.
+int pixel_blocks(size_t quads) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    return n > 0 ? n : 152;
+  }();
+  const size_t need = (quads + 255) / 256;
+  const size_t want = std::max<size_t>(1, (size_t)(8 * sms) / 3);
+  return (int)std::max<size_t>(1, std::min(need, want));
+}
+
 cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   const Plan &p = *a.plan;
   char *ws = a.ws;
@@ -3040,7 +3059,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   {
     const size_t plane = (size_t)a.H * a.W;
     if (quad_path(a.W, a.maps, rho)) {
-      const int bx = (int)std::min<size_t>((plane / 4 + 255) / 256, 8192);
+      const int bx = pixel_blocks(plane / 4);
       LaunchScope ls_("divergence", st);
       launch_k(divergence4_kernel, dim3(bx, a.C), 256, 0, st, d, ctrl);
     } else {
@@ -3157,7 +3176,7 @@ cudaError_t run_poisson(const PoissonArgs &a, cudaStream_t st) {
   {
     const size_t plane = (size_t)a.H * a.W;
     if (quad_path(a.W, a.image, rho)) {
-      const int bx = (int)std::min<size_t>((plane / 4 + 255) / 256, 8192);
+      const int bx = pixel_blocks(plane / 4);
       LaunchScope ls_("finalize", st);
       launch_k(finalize4_kernel, dim3(bx, a.C), 256, 0, st, fa, ctrl);
     } else {
