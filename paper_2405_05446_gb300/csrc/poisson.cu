@@ -44,6 +44,11 @@
 // channel, entirely in shared memory; it also solves the coarsest grid with
 // the cached FP64 inverse.
 //
+// With even widths and V(2, 1), the finest level's down pass and the up passes
+// of levels 0-2 run as streaming warps instead of tiles (see the section on
+// them below): a warp owns a 64-column strip and carries every stage of its
+// pass down a segment of rows in registers, one row per step.
+//
 // Convergence is decided on the device, so the cycle loop runs as a CUDA graph
 // with a WHILE node: no launch is spent after convergence.
 #include <stdlib.h>
