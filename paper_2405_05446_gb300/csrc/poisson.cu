@@ -2583,7 +2583,7 @@ cudaError_t launch_mg_up_t(const LvArgs &a, Ctrl *ctrl, int k, int C, cudaStream
 
 inline bool small_level(const LevelGeom &g) { return g.plane < kSmallLevel; }
 
-// Streaming finest-level passes (W even, V(2, 1)); GDGS_STREAM=0 keeps the tiles.
+// Streaming passes (even widths, V(2, 1)); GDGS_STREAM=0 keeps the tiles on every level.
 bool stream_enabled() {
   static const bool on = [] {
     const char *v = getenv("GDGS_STREAM");
