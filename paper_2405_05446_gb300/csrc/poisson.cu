@@ -997,7 +997,7 @@ constexpr int kStripX = 4;           // halo columns on each side of a strip's o
 constexpr int kStripOut = kStripW - 2 * kStripX;
 constexpr int kStreamThreads = 128;  // four independent warps per CTA
 constexpr int kStreamPre = 4;        // rows loaded ahead of their use, per stream (up pass)
-constexpr int kStreamPreDown = 8;    // the same for the down pass's one input stream
+constexpr int kStreamPreDown = 4;    // the same for the down pass's one input stream
 
 struct StreamGrid {
   int nstrips, nseg, S;  // strips of kStripOut output columns, segments of S output rows (S % 8 == 0)
